@@ -1,0 +1,336 @@
+"""Benchmark: phase-space point updates per second of the fused BGK step.
+
+One benchmark "step" is one whole run of the workload: reset the state to
+the seeded initial condition, then the workload's number of time steps
+(each: streaming, moments, Maxwellian, relaxation, boundaries).  Default
+workload: the 2D lid-driven cavity, Kn 0.1, lid Mach 0.1, 64x64 cells, 32x32
+velocities, FP64, 5000 time steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on
+the host cores instead (bounded samples of the same workload).  With N > 1
+(under torch.distributed.run) every rank runs its own replica of the
+workload (the single-GPU path does not shard here); value sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase-space updates/s (Nx*Nv per step) & % HBM roofline; mixed vs FP64 at stated err"
+UNIT = "updates/s"
+FP64_NOMINAL_FLOPS = 1.25e12   # GB300 FP64 peak from the unit counts and clocks (nominal)
+# Algorithmic FP64 flops per point update (g and h at one (cell, velocity)),
+# FMA = 2: stream 2 x (mul + 2 fma) = 10, moments 1 + 2 + 2 + 3 = 8,
+# relaxation 2 x (mul + fma) = 6 (2D); 1D: stream 6, moments 6, relaxation 6.
+FLOPS_PER_UPDATE = {1: 18.0, 2: 24.0}
+BYTES_PER_UPDATE = {"f64": 32.0}  # read f^n once, write f^{n+1} once (g and h)
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if self.proc is None or not getattr(self, "out", ""):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(name: str) -> dict:
+    from paper_0903_4044_gb300 import workloads as W
+
+    if name in ("cavity64", W.CAVITY_64["name"]):
+        return W.CAVITY_64
+    if name in ("shock", W.SHOCK_M2["name"]):
+        return W.SHOCK_M2
+    if name in ("cavity256_f64", "cavity256"):
+        return W.scaled(W.CAVITY_256, steps=200, name="cavity_kn0.05_ma0.05_256x256_v48x48_f64_200steps")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def sizes(w: dict) -> tuple[int, int, int]:
+    if w["kind"] == "shock":
+        return w["nx"], w["nvx"], 1
+    return w["n"] * w["n"], w["nv"] * w["nv"], 2
+
+
+# --------------------------------------------------------------------------
+# CPU oracle legs (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------
+def oracle_sample(w: dict, sample_steps: int):
+    """Time `sample_steps` oracle time steps of workload w; returns (updates/s, seconds, threads)."""
+    import oracle
+    from paper_0903_4044_gb300 import workloads as W
+
+    oracle.build()
+    if w["kind"] == "shock":
+        prob, g, h = oracle.shock_problem(**w)
+    else:
+        prob0, _, _ = oracle.cavity_problem(**w)
+        xi = W.perturbation(w.get("seed", 0), prob0.ncell, prob0.nv)
+        prob, g, h = oracle.cavity_problem(**w, xi=xi)
+    t0 = time.perf_counter()
+    oracle.step(prob, g, h, sample_steps)
+    dt = time.perf_counter() - t0
+    return prob.ncell * prob.nv * sample_steps / dt, dt, oracle.threads()
+
+
+def reference_arm(args, w, rank, pg):
+    if rank != 0:
+        return
+    ncell, nv, dim = sizes(w)
+    sample_steps = max(1, int(2.0e8 // (ncell * nv)))  # a few seconds per sample
+    for _ in range(args.warmup):
+        oracle_sample(w, max(1, sample_steps // 4))
+    times = []
+    rate = threads = None
+    for _ in range(args.steps):
+        rate, dt, threads = oracle_sample(w, sample_steps)
+        times.append(dt)
+    total = sum(times)
+    value = ncell * nv * sample_steps * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "sample_time_steps": sample_steps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{sample_steps} time steps of {w['name']} per benchmark step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def ours_arm(args, w, world, rank, local, pg):
+    import torch
+
+    from paper_0903_4044_gb300 import bgk as B
+    from paper_0903_4044_gb300 import build, solver
+    from paper_0903_4044_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    ncell, nv, dim = sizes(w)
+    nsteps = w["steps"]
+
+    if w["kind"] == "shock":
+        s = solver.make_shock(w, stream=stream.cuda_stream)
+    else:
+        xi = W.perturbation(w.get("seed", 0), ncell, nv)
+        s = solver.make_cavity(w, xi=xi, stream=stream.cuda_stream)
+    f0_host = torch.empty((ncell, nv, 2), dtype=torch.float64, pin_memory=True)
+    B.bgk_get_state(s.h, f0_host.numpy())
+    f0_dev = f0_host.to(f"cuda:{local}")
+    mom_host = torch.empty((ncell, 4), dtype=torch.float64, pin_memory=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    def one_step(ev=None):
+        B.bgk_set_state(s.h, f0_dev)
+        if ev is not None:
+            ev[0].record(stream)
+        B.bgk_step(s.h, nsteps)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize()
+
+    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(pg)
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for k in range(args.steps):
+            flush.zero_()           # L2 flush between timed steps (256 MB write)
+            one_step(pairs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+    B.bgk_sync(s.h)
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    elapsed = max_over_ranks(pg, elapsed)
+    kernel_s = sum(a.elapsed_time(b) for a, b in pairs) / 1e3
+    launches = args.steps * nsteps
+    per_launch = kernel_s / launches
+    updates = ncell * nv * nsteps * args.steps
+    value = world * updates / elapsed
+
+    # end to end through the C ABI with host buffers (pinned)
+    def e2e_step():
+        B.bgk_set_state(s.h, f0_host.numpy())       # H2D, synchronous on the source
+        B.bgk_step(s.h, nsteps)
+        B.bgk_moments(s.h, mom_host.numpy(), 0)     # D2H, synchronises
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+    barrier(pg)
+    e2e = {"value": world * updates / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(f0_host.numel() * 8), "d2h_bytes_per_step": int(mom_host.numel() * 8)}
+
+    peaks = load_peaks()
+    bytes_launch = BYTES_PER_UPDATE["f64"] * ncell * nv
+    flops_launch = FLOPS_PER_UPDATE[dim] * ncell * nv
+    hbm_achieved = bytes_launch / per_launch / 1e9
+    alu_achieved = flops_launch / per_launch / 1e12
+    t_hbm = bytes_launch / (peaks["hbm_gbs"] * 1e9)
+    t_alu = flops_launch / FP64_NOMINAL_FLOPS
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": alu_achieved, "peak": FP64_NOMINAL_FLOPS / 1e12,
+                "unit": "TFLOP/s", "frac": alu_achieved / (FP64_NOMINAL_FLOPS / 1e12),
+                "peak_source": "nominal FP64 (unit counts x clock)"}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peaks["source"]}
+    roof.update({"traffic": args.traffic, "kernel": "bgk::step_f64_kernel",
+                 "launch_ms": per_launch * 1e3, "hbm_gbs": hbm_achieved,
+                 "hbm_frac": hbm_achieved / peaks["hbm_gbs"], "fp64_tflops": alu_achieved})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = max(1, int(1.0e9 // (ncell * nv)))
+        rate, dt, threads = oracle_sample(w, sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{sample} time steps of {w['name']} ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "cells": ncell, "velocities": nv, "time_steps": nsteps,
+                       "precision": "f64", "parallelism": f"replica x{world}",
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="cavity64")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the step kernel from an ncu capture")
+    args = ap.parse_args()
+    world, rank, local, pg = dist_setup()
+    w = workload(args.workload)
+    if args.impl == "reference":
+        reference_arm(args, w, rank, pg)
+    else:
+        ours_arm(args, w, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

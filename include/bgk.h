@@ -1,0 +1,207 @@
+/*
+ * bgk.h - C ABI of libbgk.so, a GB300 (sm_103a) solver for the BGK model
+ * kinetic equation on a regular phase-space grid.
+ *
+ * The method is the split step of Frezzotti, Ghiroldi, Gibelli, "Solving
+ * Kinetic Equations on GPUs I: Model Kinetic Equations", Sec. 2.1: a
+ * first-order upwind free-streaming sub-step (Eq. upwind, with the integer
+ * Courant shift of Eq. exact), then per spatial cell the moments of
+ * Eq. (macroscopic), the local Maxwellian of Eq. (Maxw) and the relaxation of
+ * Eq. (relaxation).  Boundaries: the far-field inflow Maxwellians of
+ * Eq. (bc_shock) and the diffuse (fully accommodating) walls of
+ * Eq. (bc_cavity) with the zero-net-mass-flux wall density below it; specular
+ * walls are added.
+ *
+ * Units (Sec. 4.1): velocity c = v / sqrt(2 R T0), temperature
+ * theta = T / T0, density n / n0, lengths in mean free paths, time in
+ * 1 / nu0.  The collision frequency of Eqs. (frequency) and (viscosity) is
+ * nu = n * theta^(1 - omega).
+ *
+ * Velocity space is reduced by integrating out the components the flow does
+ * not depend on (the reduction cited at the end of Sec. 4.1 and in Sec. 6):
+ *   dim 1: g(x, c_x) = int f dc_y dc_z,  h = int (c_y^2 + c_z^2) f dc_y dc_z
+ *   dim 2: g(x, y, c_x, c_y) = int f dc_z,  h = int c_z^2 f dc_z
+ * One "point" of the phase space is one (cell, velocity) pair; it holds g
+ * and h.
+ *
+ * STATE LAYOUT (the layout of every state buffer crossing this ABI):
+ *   double f[ny][nx][nvy][nvx][2], component 0 = g, 1 = h;
+ *   cell = iy*nx + ix, velocity v = jy*nvx + jx (jx fastest);
+ *   cell centres x = x0 + (ix + 1/2) lx/nx, c_x = vx_min + (jx + 1/2) dcx.
+ * For dim 1, ny = nvy = 1.
+ *
+ * CONVENTIONS
+ *  - Every function returns bgk_status; nothing throws or aborts across the
+ *    ABI.  On failure bgk_last_error() describes the cause.
+ *  - The library owns the device state buffers of a solver.  The caller owns
+ *    every array passed in or out; "on_device" flags say whether a pointer is
+ *    a device pointer (non-zero) or a host pointer (zero).
+ *  - Work is enqueued on the stream given in bgk_config.cuda_stream (NULL is
+ *    the legacy default stream).  bgk_step is asynchronous; bgk_moments,
+ *    bgk_wall_fluxes, bgk_get_state and bgk_sync synchronise that stream and
+ *    report numerical failures detected by the kernels (BGK_ERR_NUMERIC).
+ *  - A solver is not thread-safe: one host thread and one stream per handle.
+ *  - The library computes in the kernels it ships for sm_103a; there is no
+ *    CPU fallback.  Without a usable GPU the calls fail with BGK_ERR_CUDA.
+ */
+#ifndef BGK_H
+#define BGK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BGK_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define BGK_API __attribute__((visibility("default")))
+#else
+#define BGK_API
+#endif
+
+typedef enum {
+  BGK_OK = 0,
+  BGK_ERR_INVALID_ARG = 1, /* bad pointer, size or configuration value */
+  BGK_ERR_UNSUPPORTED = 2, /* valid request this build does not implement */
+  BGK_ERR_OOM = 3,         /* device or host allocation failed */
+  BGK_ERR_CUDA = 4,        /* CUDA runtime error (no device, launch failure) */
+  BGK_ERR_NUMERIC = 5,     /* a cell produced n <= 0, theta <= 0, a non-finite
+                              moment, or the effective-parameter iteration
+                              failed; the state is then not trustworthy */
+  BGK_ERR_TIMEOUT = 6      /* a bounded wait inside a kernel ran out */
+} bgk_status;
+
+typedef enum {
+  BGK_F64 = 0,     /* state stored and computed in FP64 */
+  BGK_F32 = 1,     /* state stored in FP32, moments accumulated in FP64 */
+  BGK_BF16_DEV = 2 /* state stored as BF16 deviation from a fixed Maxwellian */
+} bgk_precision;
+
+typedef enum {
+  BGK_BC_INFLOW = 0,  /* Eq. (bc_shock): Maxwellian (n, ux, uy, theta) enters */
+  BGK_BC_DIFFUSE = 1, /* Eq. (bc_cavity): wall velocity (ux, uy), temperature
+                         theta; n is ignored (n_W from zero net mass flux) */
+  BGK_BC_SPECULAR = 2 /* mirror reflection; needs a velocity grid symmetric
+                         about 0 in the wall-normal component */
+} bgk_bc_kind;
+
+typedef enum { BGK_FACE_XLO = 0, BGK_FACE_XHI = 1, BGK_FACE_YLO = 2, BGK_FACE_YHI = 3 } bgk_face;
+
+typedef struct {
+  int32_t kind; /* bgk_bc_kind */
+  int32_t reserved;
+  double n, ux, uy, theta;
+} bgk_bc;
+
+typedef struct {
+  int32_t dim;          /* 1 or 2 spatial dimensions */
+  int32_t nx, ny;       /* cells; ny must be 1 when dim = 1 */
+  int32_t nvx, nvy;     /* velocity cells; nvy must be 1 when dim = 1 */
+  int32_t conservative; /* 1: Maxwellian built from effective parameters whose
+                           discrete moments equal the cell's (Sec. 2.1,
+                           remark after Eq. exact): exact conservation */
+  int32_t relax_exact;  /* 1: Eq. (relaxation); 0: f += dt nu (Phi - f) */
+  int32_t precision;    /* bgk_precision */
+  double x0, lx;        /* domain [x0, x0 + lx] */
+  double y0, ly;        /* domain [y0, y0 + ly] (dim 2) */
+  double vx_min, vx_max;
+  double vy_min, vy_max; /* dim 2 */
+  double omega;         /* viscosity exponent: nu = n theta^(1 - omega) */
+  double dt;            /* time step; 0 = derive from cfl */
+  double cfl;           /* dim 1: max|c_x| dt/dx; dim 2: (max|c_x|/dx +
+                           max|c_y|/dy) dt */
+  bgk_bc bc[4];         /* per face, indexed by bgk_face (dim 1: XLO, XHI) */
+  void* cuda_stream;    /* cudaStream_t; NULL = legacy default stream */
+} bgk_config;
+
+typedef struct {
+  double dt, dx, dy, dcx, dcy, dv; /* dv = velocity-cell volume (reduced) */
+  double max_courant;              /* dim 1: max|C|; dim 2: max(|Cx|+|Cy|) */
+  int64_t ncell, nv;               /* spatial cells, velocities per cell */
+  int64_t state_doubles;           /* ncell * nv * 2 */
+  int64_t steps_done;              /* steps enqueued since the last init */
+  int64_t device_bytes;            /* device memory held by the solver */
+  int32_t precision;
+  int32_t reserved;
+} bgk_info;
+
+typedef struct bgk_solver bgk_solver;
+
+/* Validate cfg (all checks happen before any CUDA call), build the grids and
+ * boundary tables on the current CUDA device, and allocate two state buffers
+ * (ping-pong) plus per-cell moment storage.  The state is zero until an
+ * init or set_state call.  *out receives the handle (NULL on failure).
+ * Errors: INVALID_ARG (bad value), UNSUPPORTED (e.g. 2D Courant number above
+ * 1, more than 4096 velocities per cell, walls with |C| > 1), OOM, CUDA. */
+BGK_API bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out);
+
+/* Free everything the solver holds (synchronises its stream first).
+ * NULL is accepted and ignored. */
+BGK_API bgk_status bgk_destroy(bgk_solver* s);
+
+/* Derived grid values and bookkeeping. */
+BGK_API bgk_status bgk_get_info(const bgk_solver* s, bgk_info* out);
+
+/* Initial step profile (Sec. 4.1, initial condition of the shock problem):
+ * cells with x < x_split get the Maxwellian of left = (n, ux, uy, theta),
+ * the others that of right.  Enqueued on the stream; resets steps_done and
+ * the numerical-error flag. */
+BGK_API bgk_status bgk_init_maxwellian_step(bgk_solver* s, double x_split, const double left[4],
+                                    const double right[4]);
+
+/* Uniform Maxwellian of state = (n, ux, uy, theta), multiplied point by point
+ * by (1 + amplitude * xi) with xi in the state layout (ncell*nv*2 doubles,
+ * host or device per xi_on_device; NULL = no perturbation).  Used for the
+ * cavity's perturbed rest state. */
+BGK_API bgk_status bgk_init_uniform(bgk_solver* s, const double state[4], const double* xi,
+                            int xi_on_device, double amplitude);
+
+/* Copy a state (STATE LAYOUT, ncell*nv*2 doubles) in or out.  get_state
+ * synchronises the stream. */
+BGK_API bgk_status bgk_set_state(bgk_solver* s, const double* f, int on_device);
+BGK_API bgk_status bgk_get_state(bgk_solver* s, double* f, int on_device);
+
+/* Enqueue nsteps time steps (stream, moments, Maxwellian, relaxation, each
+ * step one fused kernel; batches of steps replay a captured CUDA graph).
+ * Asynchronous.  nsteps = 0 is a no-op; negative is INVALID_ARG. */
+BGK_API bgk_status bgk_step(bgk_solver* s, int64_t nsteps);
+
+/* Per-cell moments mom[cell][4] = (n, ux, uy, theta) of Eq. (macroscopic).
+ * which = 0: of the current state; which = 1: of the post-streaming state of
+ * the last step (the values the relaxation used).  Synchronises. */
+BGK_API bgk_status bgk_moments(bgk_solver* s, int which, double* mom, int on_device);
+
+/* Fluxes through one face for each of its cells (ny cells for x faces, nx
+ * for y faces; 1 for dim 1), out[k][4] = (mass, shear, normal momentum,
+ * energy) = sum over velocities of (c_n, c_t c_n, c_n^2, c_n (|c|^2 g + h))
+ * times the crossing value times dv, where c_n is along the inward normal
+ * (+x at XLO, -x at XHI, +y at YLO, -y at YHI) and c_t is c_y on x faces,
+ * c_x on y faces.  The crossing value is the wall-adjacent cell's state for
+ * c_n < 0 and the boundary value the next step would use for c_n > 0.
+ * Synchronises. */
+BGK_API bgk_status bgk_wall_fluxes(bgk_solver* s, int face, double* out, int on_device);
+
+/* Wait for the solver's stream; report a kernel-detected numerical failure. */
+BGK_API bgk_status bgk_sync(bgk_solver* s);
+
+/* Rankine-Hugoniot states of Eq. (RH) for upstream Mach number mach with the
+ * normalisation of Sec. 4.1 (n- = 1, theta- = 1, u- = mach*sqrt(gamma/2)):
+ * up and down receive (n, u, 0, theta).  Host-only arithmetic. */
+BGK_API bgk_status bgk_rankine_hugoniot(double mach, double gamma, double up[4], double down[4]);
+
+/* Message of the calling thread's last failure ("" if none); never NULL. */
+BGK_API const char* bgk_last_error(void);
+
+/* Name of a status code; never NULL. */
+BGK_API const char* bgk_status_string(bgk_status st);
+
+/* BGK_ABI_VERSION of the loaded library. */
+BGK_API int bgk_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BGK_H */

@@ -1,0 +1,573 @@
+// bgk_api.cu - host runtime and C ABI of libbgk.so (declared in bgk.h).
+//
+// A solver holds two device state buffers (ping-pong), per-cell moment
+// storage, the per-velocity tables and a device error flag.  bgk_step
+// enqueues one fused kernel per time step; runs of kChunk steps replay a
+// CUDA graph captured once per starting buffer.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "bgk.h"
+#include "bgk_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bgk_status fail(bgk_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+bgk_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(BGK_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(BGK_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+constexpr int kChunk = 64;  // steps per captured graph (even: ends on the same buffer)
+
+}  // namespace
+
+struct bgk_solver {
+  bgk_config cfg;
+  bgk::Params P;
+  int device = 0;
+  cudaStream_t stream = nullptr;      // caller's stream (may be the legacy default)
+  cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+  double2* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  double4_32a* mom_step = nullptr;  // moments of the last post-streaming state
+  double4_32a* mom_tmp = nullptr;   // scratch for bgk_moments(which = 0)
+  double4_32a* flux_tmp = nullptr;  // scratch for bgk_wall_fluxes
+  double* cx = nullptr;
+  double* cy = nullptr;
+  double4_32a* coef = nullptr;
+  int* shift = nullptr;
+  double2* ghost = nullptr;
+  double* emitted = nullptr;
+  int* err = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int64_t steps_done = 0;
+  int64_t device_bytes = 0;
+  double max_courant = 0.0;
+
+  bgk::Tables tables() const {
+    bgk::Tables T;
+    T.cx = cx;
+    T.cy = cy;
+    T.coef = coef;
+    T.shift = shift;
+    T.ghost = ghost;
+    T.emitted = emitted;
+    return T;
+  }
+  size_t state_elems() const { return (size_t)P.nx * P.ny * P.nv; }  // (g,h) pairs
+};
+
+namespace {
+
+bool finite_all(std::initializer_list<double> v) {
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+double max_abs_centre(double vmin, double vmax, int n) {
+  const double dc = (vmax - vmin) / n;
+  double m = 0.0;
+  for (int j = 0; j < n; ++j) m = std::fmax(m, std::fabs(vmin + (j + 0.5) * dc));
+  return m;
+}
+
+// All configuration checks, before any CUDA call.  Fills P and max_courant.
+bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
+  if (c->dim != 1 && c->dim != 2) return fail(BGK_ERR_INVALID_ARG, "dim must be 1 or 2 (got %d)", c->dim);
+  if (c->nx < 1) return fail(BGK_ERR_INVALID_ARG, "nx must be >= 1 (got %d)", c->nx);
+  if (c->dim == 1 && c->ny != 1) return fail(BGK_ERR_INVALID_ARG, "ny must be 1 when dim = 1 (got %d)", c->ny);
+  if (c->dim == 2 && c->ny < 1) return fail(BGK_ERR_INVALID_ARG, "ny must be >= 1 (got %d)", c->ny);
+  if (c->nvx < 2) return fail(BGK_ERR_INVALID_ARG, "nvx must be >= 2 (got %d)", c->nvx);
+  if (c->dim == 1 && c->nvy != 1) return fail(BGK_ERR_INVALID_ARG, "nvy must be 1 when dim = 1 (got %d)", c->nvy);
+  if (c->dim == 2 && c->nvy < 2) return fail(BGK_ERR_INVALID_ARG, "nvy must be >= 2 (got %d)", c->nvy);
+  const int64_t nv = (int64_t)c->nvx * c->nvy;
+  if (nv > bgk::kMaxNv)
+    return fail(BGK_ERR_UNSUPPORTED, "nvx*nvy = %lld exceeds the %d velocities one CTA handles",
+                (long long)nv, bgk::kMaxNv);
+  if ((int64_t)c->nx * c->ny > (int64_t)0x7fffffff)
+    return fail(BGK_ERR_UNSUPPORTED, "more than 2^31-1 spatial cells");
+  if (!finite_all({c->x0, c->lx, c->vx_min, c->vx_max, c->omega, c->dt, c->cfl}))
+    return fail(BGK_ERR_INVALID_ARG, "non-finite configuration value");
+  if (!(c->lx > 0.0)) return fail(BGK_ERR_INVALID_ARG, "lx must be > 0");
+  if (!(c->vx_max > c->vx_min)) return fail(BGK_ERR_INVALID_ARG, "vx_max must exceed vx_min");
+  if (c->dim == 2) {
+    if (!finite_all({c->y0, c->ly, c->vy_min, c->vy_max}))
+      return fail(BGK_ERR_INVALID_ARG, "non-finite configuration value");
+    if (!(c->ly > 0.0)) return fail(BGK_ERR_INVALID_ARG, "ly must be > 0");
+    if (!(c->vy_max > c->vy_min)) return fail(BGK_ERR_INVALID_ARG, "vy_max must exceed vy_min");
+  }
+  if (c->dt < 0.0) return fail(BGK_ERR_INVALID_ARG, "dt must be >= 0");
+  if (c->dt == 0.0 && !(c->cfl > 0.0)) return fail(BGK_ERR_INVALID_ARG, "dt = 0 needs cfl > 0");
+  if (c->conservative != 0 && c->conservative != 1) return fail(BGK_ERR_INVALID_ARG, "conservative must be 0 or 1");
+  if (c->relax_exact != 0 && c->relax_exact != 1) return fail(BGK_ERR_INVALID_ARG, "relax_exact must be 0 or 1");
+  if (c->precision != BGK_F64) {
+    if (c->precision == BGK_F32 || c->precision == BGK_BF16_DEV)
+      return fail(BGK_ERR_UNSUPPORTED, "precision %d is not built yet", c->precision);
+    return fail(BGK_ERR_INVALID_ARG, "unknown precision %d", c->precision);
+  }
+
+  bgk::Params& p = *P;
+  std::memset(&p, 0, sizeof(p));
+  p.dim = c->dim;
+  p.nx = c->nx;
+  p.ny = c->dim == 2 ? c->ny : 1;
+  p.nvx = c->nvx;
+  p.nvy = c->dim == 2 ? c->nvy : 1;
+  p.nv = (int)nv;
+  p.conservative = c->conservative;
+  p.relax_exact = c->relax_exact;
+  p.dx = c->lx / c->nx;
+  p.dy = c->dim == 2 ? c->ly / c->ny : 1.0;
+  p.dcx = (c->vx_max - c->vx_min) / c->nvx;
+  p.dcy = c->dim == 2 ? (c->vy_max - c->vy_min) / c->nvy : 1.0;
+  p.dv = c->dim == 2 ? p.dcx * p.dcy : p.dcx;
+  p.x0 = c->x0;
+  p.vx_min = c->vx_min;
+  p.vy_min = c->dim == 2 ? c->vy_min : 0.0;
+  p.omega = c->omega;
+  const double mx = max_abs_centre(c->vx_min, c->vx_max, c->nvx);
+  const double my = c->dim == 2 ? max_abs_centre(c->vy_min, c->vy_max, c->nvy) : 0.0;
+  if (c->dt > 0.0) {
+    p.dt = c->dt;
+  } else if (c->dim == 1) {
+    p.dt = c->cfl * p.dx / mx;
+  } else {
+    p.dt = c->cfl / (mx / p.dx + my / p.dy);
+  }
+  *max_courant = c->dim == 1 ? mx * p.dt / p.dx : mx * p.dt / p.dx + my * p.dt / p.dy;
+
+  const int nfaces = c->dim == 2 ? 4 : 2;
+  bool walls = false;
+  for (int face = 0; face < bgk::kFaces; ++face) {
+    const bgk_bc& b = c->bc[face];
+    p.bc_kind[face] = b.kind;
+    p.bc_state[face][0] = b.n;
+    p.bc_state[face][1] = b.ux;
+    p.bc_state[face][2] = b.uy;
+    p.bc_state[face][3] = b.theta;
+    if (face >= nfaces) continue;
+    const bool xface = face < 2;
+    if (!finite_all({b.n, b.ux, b.uy, b.theta}))
+      return fail(BGK_ERR_INVALID_ARG, "face %d: non-finite boundary state", face);
+    if (c->dim == 1 && b.uy != 0.0)
+      return fail(BGK_ERR_INVALID_ARG, "face %d: uy must be 0 in 1D", face);
+    switch (b.kind) {
+      case BGK_BC_INFLOW:
+        if (!(b.n > 0.0) || !(b.theta > 0.0))
+          return fail(BGK_ERR_INVALID_ARG, "face %d: inflow needs n > 0 and theta > 0", face);
+        break;
+      case BGK_BC_DIFFUSE:
+        walls = true;
+        if (!(b.theta > 0.0)) return fail(BGK_ERR_INVALID_ARG, "face %d: wall theta must be > 0", face);
+        if ((xface && b.ux != 0.0) || (!xface && b.uy != 0.0))
+          return fail(BGK_ERR_INVALID_ARG, "face %d: wall velocity must be tangential", face);
+        break;
+      case BGK_BC_SPECULAR: {
+        walls = true;
+        const double lo = xface ? c->vx_min : c->vy_min, hi = xface ? c->vx_max : c->vy_max;
+        if (std::fabs(lo + hi) > 1e-12 * std::fabs(hi))
+          return fail(BGK_ERR_INVALID_ARG,
+                      "face %d: specular walls need a velocity grid symmetric about 0", face);
+        break;
+      }
+      default:
+        return fail(BGK_ERR_INVALID_ARG, "face %d: unknown boundary kind %d", face, b.kind);
+    }
+  }
+  if (c->dim == 2 && *max_courant > 1.0 + 1e-12)
+    return fail(BGK_ERR_UNSUPPORTED, "2D donor cell needs (max|cx|/dx + max|cy|/dy) dt <= 1 (got %.6g)",
+                *max_courant);
+  if (walls && *max_courant > 1.0 + 1e-12)
+    return fail(BGK_ERR_UNSUPPORTED, "walls need a Courant number <= 1 (got %.6g)", *max_courant);
+  return BGK_OK;
+}
+
+template <typename T>
+cudaError_t dev_alloc(bgk_solver* s, T** p, size_t count) {
+  const size_t bytes = sizeof(T) * (count ? count : 1);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess) s->device_bytes += (int64_t)bytes;
+  return e;
+}
+
+void release(bgk_solver* s) {
+  if (!s) return;
+  for (auto& g : s->graph)
+    if (g) cudaGraphExecDestroy(g);
+  void* bufs[] = {s->f[0], s->f[1], s->mom_step, s->mom_tmp, s->flux_tmp, s->cx, s->cy,
+                  s->coef, s->shift, s->ghost, s->emitted, s->err};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  delete s;
+}
+
+cudaError_t enqueue_step(bgk_solver* s, int from, cudaStream_t st) {
+  return bgk::launch_step_f64(s->P, s->tables(), s->f[from], s->f[1 - from], s->mom_step, s->err, st);
+}
+
+bgk_status ensure_graph(bgk_solver* s, int start) {
+  if (s->graph[start]) return BGK_OK;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture begin");
+  int b = start;
+  cudaError_t le = cudaSuccess;
+  for (int i = 0; i < kChunk && le == cudaSuccess; ++i) {
+    le = enqueue_step(s, b, s->cap_stream);
+    b ^= 1;
+  }
+  e = cudaStreamEndCapture(s->cap_stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(le, "step launch during capture");
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
+  e = cudaGraphInstantiate(&s->graph[start], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    s->graph[start] = nullptr;
+    return cuda_fail(e, "graph instantiate");
+  }
+  return BGK_OK;
+}
+
+bgk_status check_flag(bgk_solver* s) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  if (h & bgk::ERR_MOMENT)
+    return fail(BGK_ERR_NUMERIC, "a cell reached n <= 0, theta <= 0 or a non-finite moment");
+  if (h & bgk::ERR_EFFECTIVE)
+    return fail(BGK_ERR_NUMERIC, "the effective-parameter iteration did not converge in a cell");
+  return BGK_OK;
+}
+
+#define BGK_GUARD_BEGIN try {
+#define BGK_GUARD_END                                                     \
+  }                                                                       \
+  catch (const std::bad_alloc&) {                                         \
+    return fail(BGK_ERR_OOM, "host allocation failed");                   \
+  }                                                                       \
+  catch (...) {                                                           \
+    return fail(BGK_ERR_INVALID_ARG, "unexpected host exception");        \
+  }
+
+bgk_status select_device(const bgk_solver* s) {
+  cudaError_t e = cudaSetDevice(s->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return BGK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bgk_abi_version(void) { return BGK_ABI_VERSION; }
+
+const char* bgk_last_error(void) { return g_last_error.c_str(); }
+
+const char* bgk_status_string(bgk_status st) {
+  switch (st) {
+    case BGK_OK: return "BGK_OK";
+    case BGK_ERR_INVALID_ARG: return "BGK_ERR_INVALID_ARG";
+    case BGK_ERR_UNSUPPORTED: return "BGK_ERR_UNSUPPORTED";
+    case BGK_ERR_OOM: return "BGK_ERR_OOM";
+    case BGK_ERR_CUDA: return "BGK_ERR_CUDA";
+    case BGK_ERR_NUMERIC: return "BGK_ERR_NUMERIC";
+    case BGK_ERR_TIMEOUT: return "BGK_ERR_TIMEOUT";
+  }
+  return "BGK_ERR_UNKNOWN";
+}
+
+bgk_status bgk_rankine_hugoniot(double mach, double gamma, double up[4], double down[4]) {
+  if (!up || !down) return fail(BGK_ERR_INVALID_ARG, "null output");
+  if (!(mach >= 1.0) || !(gamma > 1.0) || !std::isfinite(mach) || !std::isfinite(gamma))
+    return fail(BGK_ERR_INVALID_ARG, "need mach >= 1 and gamma > 1");
+  // Eq. (RH) with n- = 1, T- = 1 and u- = M sqrt(gamma/2) (units of sqrt(2RT-)).
+  const double m2 = mach * mach;
+  const double dens = 4.0 * m2 / (m2 + 3.0);
+  const double temp = (5.0 * m2 - 1.0) * (m2 + 3.0) / (16.0 * m2);
+  up[0] = 1.0;
+  up[1] = mach * std::sqrt(0.5 * gamma);
+  up[2] = 0.0;
+  up[3] = 1.0;
+  down[0] = dens;
+  down[1] = up[1] / dens;
+  down[2] = 0.0;
+  down[3] = temp;
+  return BGK_OK;
+}
+
+bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
+  BGK_GUARD_BEGIN
+  if (!out) return fail(BGK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(BGK_ERR_INVALID_ARG, "cfg is NULL");
+  bgk::Params P;
+  double maxc = 0.0;
+  bgk_status st = validate(cfg, &P, &maxc);
+  if (st != BGK_OK) return st;
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(BGK_ERR_UNSUPPORTED, "libbgk is built for sm_103a only (device %s is sm_%d%d)",
+                prop.name, prop.major, prop.minor);
+
+  bgk_solver* s = new bgk_solver();
+  s->cfg = *cfg;
+  s->P = P;
+  s->device = dev;
+  s->stream = (cudaStream_t)cfg->cuda_stream;
+  s->max_courant = maxc;
+  const size_t elems = s->state_elems();
+  const size_t ncell = (size_t)P.nx * P.ny;
+  const int nfc = P.nx > P.ny ? P.nx : P.ny;
+#define ALLOC(ptr, n)                                  \
+  do {                                                 \
+    cudaError_t ae = dev_alloc(s, &s->ptr, (n));       \
+    if (ae != cudaSuccess) {                           \
+      bgk_status rs = cuda_fail(ae, "allocate " #ptr); \
+      release(s);                                      \
+      return rs;                                       \
+    }                                                  \
+  } while (0)
+  ALLOC(f[0], elems);
+  ALLOC(f[1], elems);
+  ALLOC(mom_step, ncell);
+  ALLOC(mom_tmp, ncell);
+  ALLOC(flux_tmp, nfc);
+  ALLOC(cx, P.nvx);
+  ALLOC(cy, P.nvy);
+  ALLOC(coef, P.nv);
+  ALLOC(shift, P.nv);
+  ALLOC(ghost, (size_t)bgk::kFaces * P.nv);
+  ALLOC(emitted, bgk::kFaces);
+  ALLOC(err, 1);
+#undef ALLOC
+  e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->f[0], 0, sizeof(double2) * elems, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->f[1], 0, sizeof(double2) * elems, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->mom_step, 0, sizeof(double4_32a) * ncell, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess)
+    e = bgk::launch_build_tables(P, s->cx, s->cy, s->coef, s->shift, s->ghost, s->emitted, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    bgk_status rs = cuda_fail(e, "solver set-up");
+    release(s);
+    return rs;
+  }
+  *out = s;
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_destroy(bgk_solver* s) {
+  if (!s) return BGK_OK;
+  BGK_GUARD_BEGIN
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  release(s);
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_get_info(const bgk_solver* s, bgk_info* out) {
+  if (!s || !out) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  out->dt = s->P.dt;
+  out->dx = s->P.dx;
+  out->dy = s->P.dy;
+  out->dcx = s->P.dcx;
+  out->dcy = s->P.dcy;
+  out->dv = s->P.dv;
+  out->max_courant = s->max_courant;
+  out->ncell = (int64_t)s->P.nx * s->P.ny;
+  out->nv = s->P.nv;
+  out->state_doubles = (int64_t)s->state_elems() * 2;
+  out->steps_done = s->steps_done;
+  out->device_bytes = s->device_bytes;
+  out->precision = s->cfg.precision;
+  return BGK_OK;
+}
+
+bgk_status bgk_init_maxwellian_step(bgk_solver* s, double x_split, const double left[4],
+                                    const double right[4]) {
+  BGK_GUARD_BEGIN
+  if (!s || !left || !right) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  for (const double* st : {left, right}) {
+    if (!(st[0] > 0.0) || !(st[3] > 0.0) || !finite_all({st[0], st[1], st[2], st[3]}))
+      return fail(BGK_ERR_INVALID_ARG, "states need finite values, n > 0 and theta > 0");
+    if (s->P.dim == 1 && st[2] != 0.0) return fail(BGK_ERR_INVALID_ARG, "uy must be 0 in 1D");
+  }
+  if (!std::isfinite(x_split)) return fail(BGK_ERR_INVALID_ARG, "x_split must be finite");
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess) e = bgk::launch_init_step(s->P, s->f[s->cur], x_split, left, right, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "init step profile");
+  s->steps_done = 0;
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_init_uniform(bgk_solver* s, const double state[4], const double* xi, int xi_on_device,
+                            double amplitude) {
+  BGK_GUARD_BEGIN
+  if (!s || !state) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  if (!(state[0] > 0.0) || !(state[3] > 0.0) || !finite_all({state[0], state[1], state[2], state[3], amplitude}))
+    return fail(BGK_ERR_INVALID_ARG, "state needs finite values, n > 0 and theta > 0");
+  if (s->P.dim == 1 && state[2] != 0.0) return fail(BGK_ERR_INVALID_ARG, "uy must be 0 in 1D");
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  const size_t bytes = sizeof(double2) * s->state_elems();
+  const double2* dxi = nullptr;
+  cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess && xi) {
+    if (xi_on_device) {
+      dxi = (const double2*)xi;
+    } else {
+      // stage the host perturbation in the idle state buffer
+      double2* stage = s->f[1 - s->cur];
+      e = cudaMemcpyAsync(stage, xi, bytes, cudaMemcpyHostToDevice, s->stream);
+      dxi = stage;
+    }
+  }
+  if (e == cudaSuccess) e = bgk::launch_init_uniform(s->P, s->f[s->cur], state, dxi, amplitude, s->stream);
+  if (e == cudaSuccess && xi && !xi_on_device) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "init uniform state");
+  s->steps_done = 0;
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_set_state(bgk_solver* s, const double* f, int on_device) {
+  BGK_GUARD_BEGIN
+  if (!s || !f) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  const size_t bytes = sizeof(double2) * s->state_elems();
+  cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->f[s->cur], f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        s->stream);
+  // a host source may be reused as soon as the call returns
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_state copy");
+  s->steps_done = 0;
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_get_state(bgk_solver* s, double* f, int on_device) {
+  BGK_GUARD_BEGIN
+  if (!s || !f) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  const size_t bytes = sizeof(double2) * s->state_elems();
+  cudaError_t e = cudaMemcpyAsync(f, s->f[s->cur], bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_state copy");
+  return check_flag(s);
+  BGK_GUARD_END
+}
+
+bgk_status bgk_step(bgk_solver* s, int64_t nsteps) {
+  BGK_GUARD_BEGIN
+  if (!s) return fail(BGK_ERR_INVALID_ARG, "null solver");
+  if (nsteps < 0) return fail(BGK_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return BGK_OK;
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  while (nsteps >= kChunk) {
+    st = ensure_graph(s, s->cur);
+    if (st != BGK_OK) return st;
+    cudaError_t e = cudaGraphLaunch(s->graph[s->cur], s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    nsteps -= kChunk;
+    s->steps_done += kChunk;
+  }
+  while (nsteps > 0) {
+    cudaError_t e = enqueue_step(s, s->cur, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step launch");
+    s->cur ^= 1;
+    --nsteps;
+    ++s->steps_done;
+  }
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_moments(bgk_solver* s, int which, double* mom, int on_device) {
+  BGK_GUARD_BEGIN
+  if (!s || !mom) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  if (which != 0 && which != 1) return fail(BGK_ERR_INVALID_ARG, "which must be 0 or 1");
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  const size_t ncell = (size_t)s->P.nx * s->P.ny;
+  cudaError_t e = cudaSuccess;
+  const double4_32a* src = s->mom_step;
+  if (which == 0) {
+    e = bgk::launch_moments(s->P, s->tables(), s->f[s->cur], s->mom_tmp, s->stream);
+    src = s->mom_tmp;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(mom, src, sizeof(double4_32a) * ncell,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "moments");
+  return check_flag(s);
+  BGK_GUARD_END
+}
+
+bgk_status bgk_wall_fluxes(bgk_solver* s, int face, double* out, int on_device) {
+  BGK_GUARD_BEGIN
+  if (!s || !out) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  const int nfaces = s->P.dim == 2 ? 4 : 2;
+  if (face < 0 || face >= nfaces) return fail(BGK_ERR_INVALID_ARG, "face %d does not exist for dim %d", face, s->P.dim);
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  const int ncells = (face < 2) ? s->P.ny : s->P.nx;
+  cudaError_t e = bgk::launch_wall_fluxes(s->P, s->tables(), s->f[s->cur], face, s->flux_tmp, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, s->flux_tmp, sizeof(double4_32a) * ncells,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "wall fluxes");
+  return check_flag(s);
+  BGK_GUARD_END
+}
+
+bgk_status bgk_sync(bgk_solver* s) {
+  BGK_GUARD_BEGIN
+  if (!s) return fail(BGK_ERR_INVALID_ARG, "null solver");
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  return check_flag(s);
+  BGK_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// bgk_internal.h - structures shared by the host runtime and the kernels of
+// libbgk.so (not part of the public ABI; see include/bgk.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bgk {
+
+constexpr int kMaxNv = 4096;   // velocities per cell handled by one CTA
+constexpr int kFaces = 4;
+enum { XLO = 0, XHI = 1, YLO = 2, YHI = 3 };
+enum { BC_INFLOW = 0, BC_DIFFUSE = 1, BC_SPECULAR = 2 };
+
+// Error bits written by kernels into the solver's device flag.
+enum { ERR_MOMENT = 1, ERR_EFFECTIVE = 2 };
+
+// Effective-parameter iteration (Sec. 2.1, remark on exact conservation):
+// p <- p + (q - D(p)) until an update is below kEffTol, at most kEffMaxIt
+// updates; a run that ends above kEffFail is a failure.
+constexpr double kEffTol = 1e-13;
+constexpr int kEffMaxIt = 20;
+constexpr double kEffFail = 1e-9;
+
+// Scalar description of one problem, passed by value to every kernel.
+struct Params {
+  int dim, nx, ny, nvx, nvy, nv;
+  int conservative, relax_exact;
+  int bc_kind[kFaces];
+  double dt, dx, dy, dcx, dcy, dv;
+  double x0, vx_min, vy_min;
+  double omega;
+  double bc_state[kFaces][4];  // n, ux, uy, theta
+};
+
+// Per-velocity tables built once on the device (build_tables).
+struct Tables {
+  const double* cx;       // [nvx] velocity-cell centres
+  const double* cy;       // [nvy] (dim 1: one entry, 0)
+  const double4_32a* coef;    // [nv] (a0, ax, ay, |c|^2): streaming weights, 2D
+                          //      (w_near, w_far, 0, c_x^2): 1D
+  const int* shift;       // [nv] 1D integer Courant shift [C] (0 in 2D)
+  const double2* ghost;   // [kFaces][nv] inflow Maxwellian, or the unit-density
+                          //   wall Maxwellian for diffuse faces
+  const double* emitted;  // [kFaces] sum_{c_n>0} c_n G_W(n=1) dv (diffuse)
+};
+
+// Launchers (bgk_step.cu, bgk_aux.cu).  All enqueue on `stream`.
+cudaError_t launch_step_f64(const Params& P, const Tables& T, const double2* fin, double2* fout,
+                            double4_32a* mom, int* err, cudaStream_t stream);
+cudaError_t launch_build_tables(const Params& P, double* cx, double* cy, double4_32a* coef, int* shift,
+                                double2* ghost, double* emitted, cudaStream_t stream);
+cudaError_t launch_init_step(const Params& P, double2* f, double x_split, const double left[4],
+                             const double right[4], cudaStream_t stream);
+cudaError_t launch_init_uniform(const Params& P, double2* f, const double state[4],
+                                const double2* xi, double amplitude, cudaStream_t stream);
+cudaError_t launch_moments(const Params& P, const Tables& T, const double2* f, double4_32a* mom,
+                           cudaStream_t stream);
+cudaError_t launch_wall_fluxes(const Params& P, const Tables& T, const double2* f, int face,
+                               double4_32a* out, cudaStream_t stream);
+
+}  // namespace bgk

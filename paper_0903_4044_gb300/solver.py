@@ -1,0 +1,129 @@
+"""A small object wrapper over the C ABI plus builders for the paper's two problems.
+
+The builders turn raw workload parameters (``workloads.py``) into a
+``bgk_config``: the 1D normal shock of Sec. 4.1 (domain [-L/2, L/2],
+Rankine-Hugoniot end states as inflow boundary values, step initial profile)
+and the lid-driven cavity of Sec. 5.1 (side 1/Kn mean free paths, isothermal
+diffuse walls, lid speed U_W = Ma sqrt(gamma/2) along +x, perturbed resting
+Maxwellian initial state).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import bgk as B
+
+GAMMA = 5.0 / 3.0  # monatomic gas
+
+
+class Solver:
+    """Owns one ``bgk_solver`` handle; frees it on close()/context exit."""
+
+    def __init__(self, cfg: B.bgk_config):
+        self.cfg = cfg
+        self.h = B.bgk_create(cfg)
+        self.info = B.bgk_get_info(self.h)
+        self.ncell = int(self.info.ncell)
+        self.nv = int(self.info.nv)
+
+    # lifetime
+    def close(self) -> None:
+        if self.h:
+            B.bgk_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state
+    def init_step(self, x_split, left, right) -> None:
+        B.bgk_init_maxwellian_step(self.h, x_split, left, right)
+
+    def init_uniform(self, state, xi=None, amplitude=0.0) -> None:
+        B.bgk_init_uniform(self.h, state, xi, amplitude)
+
+    def set_state(self, f) -> None:
+        B.bgk_set_state(self.h, f)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((self.ncell, self.nv, 2))
+        B.bgk_get_state(self.h, out)
+        return out
+
+    # stepping and outputs
+    def step(self, n: int) -> None:
+        B.bgk_step(self.h, n)
+
+    def sync(self) -> None:
+        B.bgk_sync(self.h)
+
+    def moments(self, which: int = 0, out=None):
+        if out is None:
+            out = np.empty((self.ncell, 4))
+        B.bgk_moments(self.h, out, which)
+        return out
+
+    def wall_fluxes(self, face: int, out=None):
+        n = (self.cfg.ny if face in (B.BGK_FACE_XLO, B.BGK_FACE_XHI) else self.cfg.nx)
+        if out is None:
+            out = np.empty((n, 4))
+        B.bgk_wall_fluxes(self.h, face, out)
+        return out
+
+    @property
+    def dt(self) -> float:
+        return self.info.dt
+
+
+def shock_config(*, mach, nx, length, nvx, vx, omega, cfl, conservative=1, relax_exact=1,
+                 precision=B.BGK_F64, stream=None, **_ignored):
+    """(cfg, up, down) for the Sec. 4.1 normal shock."""
+    up, down = B.bgk_rankine_hugoniot(mach, GAMMA)
+    bc = [(B.BGK_BC_INFLOW, *up), (B.BGK_BC_INFLOW, *down)]
+    cfg = B.make_config(dim=1, nx=nx, ny=1, x0=-0.5 * length, lx=length, nvx=nvx, nvy=1, vx=vx,
+                        omega=omega, cfl=cfl, conservative=conservative, relax_exact=relax_exact,
+                        precision=precision, bc=bc, stream=stream)
+    return cfg, up, down
+
+
+def cavity_config(*, kn, lid_mach, n, nv, vbox, omega, cfl, conservative=1, relax_exact=1,
+                  precision=B.BGK_F64, wall="diffuse", stream=None, **_ignored):
+    """cfg for the Sec. 5.1 lid-driven cavity (lid at y = L moving along +x)."""
+    side = 1.0 / kn
+    uw = lid_mach * math.sqrt(GAMMA / 2.0)
+    kind = B.BGK_BC_DIFFUSE if wall == "diffuse" else B.BGK_BC_SPECULAR
+    rest = (kind, 1.0, 0.0, 0.0, 1.0)
+    lid = (kind, 1.0, uw, 0.0, 1.0)
+    return B.make_config(dim=2, nx=n, ny=n, lx=side, ly=side, nvx=nv, nvy=nv, vx=vbox, vy=vbox,
+                         omega=omega, cfl=cfl, conservative=conservative, relax_exact=relax_exact,
+                         precision=precision, bc=[rest, rest, rest, lid], stream=stream)
+
+
+def make_shock(w: dict, stream=None, **over) -> Solver:
+    """Solver for a shock workload, initialised with the step profile at x = 0."""
+    cfg, up, down = shock_config(**{**w, **over}, stream=stream)
+    s = Solver(cfg)
+    s.init_step(0.0, up, down)
+    s.up, s.down = up, down
+    return s
+
+
+def make_cavity(w: dict, xi=None, stream=None, **over) -> Solver:
+    """Solver for a cavity workload, initialised to the resting Maxwellian
+    times (1 + amp*xi) (xi in the state layout, host array or CUDA tensor)."""
+    p = {**w, **over}
+    s = Solver(cavity_config(**p, stream=stream))
+    s.init_uniform((1.0, 0.0, 0.0, 1.0), xi, p.get("amp", 0.0) if xi is not None else 0.0)
+    return s
