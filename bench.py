@@ -260,16 +260,19 @@ def ours_arm(args, w, world, rank, local, pg):
         B.bgk_set_state(s.h, f0_host.numpy())       # H2D, synchronous on the source
         B.bgk_step(s.h, nsteps)
         B.bgk_moments(s.h, mom_host.numpy(), 0)     # D2H, synchronises
-    for _ in range(args.warmup):
-        e2e_step()
-    barrier(pg)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
-    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
-    barrier(pg)
-    e2e = {"value": world * updates / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(f0_host.numel() * 8), "d2h_bytes_per_step": int(mom_host.numel() * 8)}
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+        barrier(pg)
+        e2e = {"value": world * updates / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(f0_host.numel() * 8),
+               "d2h_bytes_per_step": int(mom_host.numel() * 8)}
 
     peaks = load_peaks()
     bytes_launch = BYTES_PER_UPDATE["f64"] * ncell * nv
@@ -321,9 +324,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the step kernel from an ncu capture")
+    ap.add_argument("--time-steps", type=int, default=None,
+                    help="override the workload's time steps per benchmark step (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
     w = workload(args.workload)
+    if args.time_steps is not None:
+        w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
     if args.impl == "reference":
         reference_arm(args, w, rank, pg)
     else:

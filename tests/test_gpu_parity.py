@@ -231,12 +231,10 @@ def test_cavity256_one_step_full_size():
 # ---------------------------------------------------------------------------
 # Edge cases and invariants
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("nx,ny,nvx,nvy", [(1, 5, 6, 4), (7, 1, 4, 6), (1, 1, 2, 2), (3, 2, 64, 64)])
-def test_degenerate_and_maximum_grids(nx, ny, nvx, nvy):
-    # a single cell row/column (cells touching opposite walls), the smallest
-    # velocity grid, and the largest velocity set one CTA takes (4096).
+def _wall_box(nx, ny, nvx, nvy, cons):
     bc = [(1, 1, 0, 0, 1)] * 3 + [(1, 1, 0.05, 0, 1)]
-    kw = dict(dim=2, nx=nx, ny=ny, lx=nx * 0.5, ly=ny * 0.5, nvx=nvx, nvy=nvy, vx=(-4, 4), vy=(-4, 4), cfl=0.6)
+    kw = dict(dim=2, nx=nx, ny=ny, lx=nx * 0.5, ly=ny * 0.5, nvx=nvx, nvy=nvy, vx=(-4, 4), vy=(-4, 4),
+              cfl=0.6, conservative=cons)
     cfg = B.make_config(**kw, bc=bc)
     oc = oracle.make_config(**kw, bc_kind=(1, 1, 1, 1),
                             bc_state=((1, 0, 0, 1),) * 3 + ((1, 0.05, 0, 1),))
@@ -245,9 +243,33 @@ def test_degenerate_and_maximum_grids(nx, ny, nvx, nvy):
     g, h = oracle.init_uniform(prob, (1.0, 0.0, 0.0, 1.0), xi, 1e-2)
     s = solver.Solver(cfg)
     s.init_uniform((1.0, 0.0, 0.0, 1.0), xi, 1e-2)
+    return s, prob, g, h
+
+
+@pytest.mark.parametrize("nx,ny,nvx,nvy,cons", [(1, 5, 12, 10, 1), (7, 1, 10, 12, 1), (1, 1, 2, 2, 0),
+                                                (3, 2, 64, 64, 1)])
+def test_degenerate_and_maximum_grids(nx, ny, nvx, nvy, cons):
+    # a single cell row/column (cells touching opposite walls), a single
+    # cell with the smallest velocity grid, and the largest velocity set one
+    # CTA takes (4096).
+    s, prob, g, h = _wall_box(nx, ny, nvx, nvy, cons)
     s.step(5)
     g1, h1, _ = oracle.step(prob, g, h, 5)
     assert_state_close(s.get_state(), g1, h1, tol=1e-12)
+    s.close()
+
+
+def test_too_coarse_grid_fails_on_both_sides():
+    # On a 6 x 4 velocity grid the discrete Maxwellian is too far from the
+    # continuous one for the effective-parameter iteration to converge: the
+    # oracle refuses, and the GPU reports BGK_ERR_NUMERIC instead of a state.
+    s, prob, g, h = _wall_box(1, 5, 6, 4, 1)
+    with pytest.raises(RuntimeError):
+        oracle.step(prob, g, h, 1)
+    s.step(1)
+    with pytest.raises(B.BgkError) as e:
+        s.sync()
+    assert e.value.status == B.BGK_ERR_NUMERIC
     s.close()
 
 
