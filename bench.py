@@ -210,10 +210,10 @@ def ours_arm(args, w, world, rank, local, pg):
     nsteps = w["steps"]
 
     if w["kind"] == "shock":
-        s = solver.make_shock(w, stream=stream.cuda_stream)
+        s = solver.make_shock(w, stream=stream.cuda_stream, tile_cells=args.tile)
     else:
         xi = W.perturbation(w.get("seed", 0), ncell, nv)
-        s = solver.make_cavity(w, xi=xi, stream=stream.cuda_stream)
+        s = solver.make_cavity(w, xi=xi, stream=stream.cuda_stream, tile_cells=args.tile)
     f0_host = torch.empty((ncell, nv, 2), dtype=torch.float64, pin_memory=True)
     B.bgk_get_state(s.h, f0_host.numpy())
     f0_dev = f0_host.to(f"cuda:{local}")
@@ -305,6 +305,7 @@ def ours_arm(args, w, world, rank, local, pg):
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "cells": ncell, "velocities": nv, "time_steps": nsteps,
+                       "tile_cells": int(s.info.tile_cells),
                        "precision": "f64", "parallelism": f"replica x{world}",
                        "l2": "flushed (256 MB write) between timed steps"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
@@ -327,6 +328,7 @@ def main():
     ap.add_argument("--time-steps", type=int, default=None,
                     help="override the workload's time steps per benchmark step (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--tile", type=int, default=0, help="cells per CTA of the step kernel (0 = library choice)")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
     w = workload(args.workload)

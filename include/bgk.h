@@ -105,6 +105,10 @@ typedef struct {
                            remark after Eq. exact): exact conservation */
   int32_t relax_exact;  /* 1: Eq. (relaxation); 0: f += dt nu (Phi - f) */
   int32_t precision;    /* bgk_precision */
+  int32_t tile_cells;   /* spatial cells per CTA of the step kernel: 0 = chosen
+                           by the library, else 1, 2, 4 or 8 (tuning knob; the
+                           results do not depend on it) */
+  int32_t reserved0;    /* must be 0 */
   double x0, lx;        /* domain [x0, x0 + lx] */
   double y0, ly;        /* domain [y0, y0 + ly] (dim 2) */
   double vx_min, vx_max;
@@ -125,7 +129,7 @@ typedef struct {
   int64_t steps_done;              /* steps enqueued since the last init */
   int64_t device_bytes;            /* device memory held by the solver */
   int32_t precision;
-  int32_t reserved;
+  int32_t tile_cells;              /* cells per CTA the step kernel uses */
 } bgk_info;
 
 typedef struct bgk_solver bgk_solver;

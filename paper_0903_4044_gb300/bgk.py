@@ -46,6 +46,7 @@ class bgk_config(ctypes.Structure):
         ("dim", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
         ("nvx", ctypes.c_int32), ("nvy", ctypes.c_int32), ("conservative", ctypes.c_int32),
         ("relax_exact", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("tile_cells", ctypes.c_int32), ("reserved0", ctypes.c_int32),
         ("x0", ctypes.c_double), ("lx", ctypes.c_double), ("y0", ctypes.c_double), ("ly", ctypes.c_double),
         ("vx_min", ctypes.c_double), ("vx_max", ctypes.c_double),
         ("vy_min", ctypes.c_double), ("vy_max", ctypes.c_double),
@@ -60,7 +61,7 @@ class bgk_info(ctypes.Structure):
         ("dcx", ctypes.c_double), ("dcy", ctypes.c_double), ("dv", ctypes.c_double),
         ("max_courant", ctypes.c_double), ("ncell", ctypes.c_int64), ("nv", ctypes.c_int64),
         ("state_doubles", ctypes.c_int64), ("steps_done", ctypes.c_int64),
-        ("device_bytes", ctypes.c_int64), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("device_bytes", ctypes.c_int64), ("precision", ctypes.c_int32), ("tile_cells", ctypes.c_int32),
     ]
 
 
@@ -125,11 +126,12 @@ def _ptr(a) -> tuple[int, int]:
 # --- configuration ---------------------------------------------------------
 def make_config(*, dim, nx, ny=1, x0=0.0, lx=1.0, y0=0.0, ly=1.0, nvx, nvy=1, vx=(-1.0, 1.0),
                 vy=(-1.0, 1.0), omega=0.5, dt=0.0, cfl=0.0, conservative=1, relax_exact=1,
-                precision=BGK_F64, bc=None, stream=None) -> bgk_config:
+                precision=BGK_F64, tile_cells=0, bc=None, stream=None) -> bgk_config:
     """Fill a bgk_config.  ``bc`` is a sequence of up to four (kind, n, ux, uy, theta)."""
     c = bgk_config()
     c.dim, c.nx, c.ny, c.nvx, c.nvy = dim, nx, ny, nvx, nvy
     c.conservative, c.relax_exact, c.precision = conservative, relax_exact, precision
+    c.tile_cells = tile_cells
     c.x0, c.lx, c.y0, c.ly = x0, lx, y0, ly
     c.vx_min, c.vx_max = vx
     c.vy_min, c.vy_max = vy

@@ -35,6 +35,8 @@ bgk_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 constexpr int kChunk = 64;  // steps per captured graph (even: ends on the same buffer)
+constexpr size_t kMaxSmem = 226 * 1024;   // dynamic shared memory one CTA may use (227 KB minus static)
+constexpr size_t kAutoSmem = 113 * 1024;  // automatic tiles leave room for two CTAs per SM
 
 }  // namespace
 
@@ -53,6 +55,8 @@ struct bgk_solver {
   double* cy = nullptr;
   double4_32a* coef = nullptr;
   int* shift = nullptr;
+  double2* cxy = nullptr;
+  int* vinfo = nullptr;
   double2* ghost = nullptr;
   double* emitted = nullptr;
   int* err = nullptr;
@@ -67,6 +71,8 @@ struct bgk_solver {
     T.cy = cy;
     T.coef = coef;
     T.shift = shift;
+    T.cxy = cxy;
+    T.vinfo = vinfo;
     T.ghost = ghost;
     T.emitted = emitted;
     return T;
@@ -118,6 +124,10 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
   if (c->dt == 0.0 && !(c->cfl > 0.0)) return fail(BGK_ERR_INVALID_ARG, "dt = 0 needs cfl > 0");
   if (c->conservative != 0 && c->conservative != 1) return fail(BGK_ERR_INVALID_ARG, "conservative must be 0 or 1");
   if (c->relax_exact != 0 && c->relax_exact != 1) return fail(BGK_ERR_INVALID_ARG, "relax_exact must be 0 or 1");
+  if (c->reserved0 != 0) return fail(BGK_ERR_INVALID_ARG, "reserved0 must be 0");
+  if (c->tile_cells != 0 && c->tile_cells != 1 && c->tile_cells != 2 && c->tile_cells != 4 &&
+      c->tile_cells != 8)
+    return fail(BGK_ERR_INVALID_ARG, "tile_cells must be 0, 1, 2, 4 or 8 (got %d)", c->tile_cells);
   if (c->precision != BGK_F64) {
     if (c->precision == BGK_F32 || c->precision == BGK_BF16_DEV)
       return fail(BGK_ERR_UNSUPPORTED, "precision %d is not built yet", c->precision);
@@ -153,6 +163,16 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
     p.dt = c->cfl / (mx / p.dx + my / p.dy);
   }
   *max_courant = c->dim == 1 ? mx * p.dt / p.dx : mx * p.dt / p.dx + my * p.dt / p.dy;
+
+  // cells per CTA: the caller's choice (checked here), else chosen in
+  // bgk_create once the device's SM count is known
+  p.tile = c->tile_cells;
+  if (c->tile_cells && bgk::step_f64_smem_bytes(p, p.tile) > kMaxSmem)
+    return fail(BGK_ERR_UNSUPPORTED, "tile_cells = %d needs %zu bytes of shared memory (max %zu)",
+                p.tile, bgk::step_f64_smem_bytes(p, p.tile), kMaxSmem);
+  if (!c->tile_cells && bgk::step_f64_smem_bytes(p, 1) > kMaxSmem)
+    return fail(BGK_ERR_UNSUPPORTED, "one cell's state needs %zu bytes of shared memory (max %zu)",
+                bgk::step_f64_smem_bytes(p, 1), kMaxSmem);
 
   const int nfaces = c->dim == 2 ? 4 : 2;
   bool walls = false;
@@ -200,6 +220,15 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
   return BGK_OK;
 }
 
+// Largest tile (cells per CTA) that keeps two CTAs' staged state within an
+// SM's shared memory and still gives every SM at least two CTAs.
+int auto_tile(const bgk::Params& P, int sms) {
+  const long long ncell = (long long)P.nx * P.ny;
+  for (int t : {8, 4, 2})
+    if (bgk::step_f64_smem_bytes(P, t) <= kAutoSmem && (ncell + t - 1) / t >= 2LL * sms) return t;
+  return 1;
+}
+
 template <typename T>
 cudaError_t dev_alloc(bgk_solver* s, T** p, size_t count) {
   const size_t bytes = sizeof(T) * (count ? count : 1);
@@ -212,8 +241,8 @@ void release(bgk_solver* s) {
   if (!s) return;
   for (auto& g : s->graph)
     if (g) cudaGraphExecDestroy(g);
-  void* bufs[] = {s->f[0], s->f[1], s->mom_step, s->mom_tmp, s->flux_tmp, s->cx, s->cy,
-                  s->coef, s->shift, s->ghost, s->emitted, s->err};
+  void* bufs[] = {s->f[0], s->f[1], s->mom_step, s->mom_tmp, s->flux_tmp, s->cx, s->cy, s->coef,
+                  s->shift, s->cxy, s->vinfo, s->ghost, s->emitted, s->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -338,6 +367,8 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
     return fail(BGK_ERR_UNSUPPORTED, "libbgk is built for sm_103a only (device %s is sm_%d%d)",
                 prop.name, prop.major, prop.minor);
 
+  if (P.tile == 0) P.tile = auto_tile(P, prop.multiProcessorCount);
+
   bgk_solver* s = new bgk_solver();
   s->cfg = *cfg;
   s->P = P;
@@ -365,6 +396,8 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
   ALLOC(cy, P.nvy);
   ALLOC(coef, P.nv);
   ALLOC(shift, P.nv);
+  ALLOC(cxy, P.nv);
+  ALLOC(vinfo, P.nv);
   ALLOC(ghost, (size_t)bgk::kFaces * P.nv);
   ALLOC(emitted, bgk::kFaces);
   ALLOC(err, 1);
@@ -375,7 +408,9 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(s->mom_step, 0, sizeof(double4_32a) * ncell, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
   if (e == cudaSuccess)
-    e = bgk::launch_build_tables(P, s->cx, s->cy, s->coef, s->shift, s->ghost, s->emitted, s->stream);
+    e = bgk::launch_build_tables(P, s->cx, s->cy, s->coef, s->shift, s->cxy, s->vinfo, s->ghost,
+                                 s->emitted, s->stream);
+  if (e == cudaSuccess) e = bgk::prepare_step_f64(P);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
     bgk_status rs = cuda_fail(e, "solver set-up");
@@ -413,6 +448,7 @@ bgk_status bgk_get_info(const bgk_solver* s, bgk_info* out) {
   out->steps_done = s->steps_done;
   out->device_bytes = s->device_bytes;
   out->precision = s->cfg.precision;
+  out->tile_cells = s->P.tile;
   return BGK_OK;
 }
 

@@ -13,7 +13,7 @@ __device__ __forceinline__ double centre(double vmin, int j, double dc) {
 
 // Per-velocity streaming weights and boundary Maxwellians.
 __global__ void tables_kernel(const Params P, double* cx, double* cy, double4_32a* coef, int* shift,
-                              double2* ghost) {
+                              double2* cxy, int* vinfo, double2* ghost) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P.nv) return;
   const int jx = j % P.nvx, jy = j / P.nvx;
@@ -22,6 +22,10 @@ __global__ void tables_kernel(const Params P, double* cx, double* cy, double4_32
   if (jy == 0) cx[jx] = cxj;
   if (jx == 0) cy[jy] = cyj;
   const double c2 = __dadd_rn(__dmul_rn(cxj, cxj), __dmul_rn(cyj, cyj));
+  cxy[j] = make_double2(cxj, cyj);
+  const int sgx = cxj > 0.0 ? 1 : (cxj < 0.0 ? -1 : 0);
+  const int sgy = cyj > 0.0 ? 1 : (cyj < 0.0 ? -1 : 0);
+  vinfo[j] = jx | (jy << 12) | ((sgx + 1) << 24) | ((sgy + 1) << 26);
   if (P.dim == 2) {
     // unsplit donor cell: f~ = (1 - |Cx| - |Cy|) f + |Cx| f_upx + |Cy| f_upy
     const double ax = fabs(cxj) * P.dt / P.dx;
@@ -71,8 +75,9 @@ __global__ void __launch_bounds__(256) emitted_kernel(const Params P, const doub
 }
 
 cudaError_t launch_build_tables(const Params& P, double* cx, double* cy, double4_32a* coef, int* shift,
-                                double2* ghost, double* emitted, cudaStream_t stream) {
-  tables_kernel<<<(P.nv + 255) / 256, 256, 0, stream>>>(P, cx, cy, coef, shift, ghost);
+                                double2* cxy, int* vinfo, double2* ghost, double* emitted,
+                                cudaStream_t stream) {
+  tables_kernel<<<(P.nv + 255) / 256, 256, 0, stream>>>(P, cx, cy, coef, shift, cxy, vinfo, ghost);
   emitted_kernel<<<1, 256, 0, stream>>>(P, cx, cy, ghost, emitted);
   return cudaGetLastError();
 }

@@ -114,94 +114,6 @@ __device__ __forceinline__ bool moments_ok(const double q[4]) {
          isfinite(q[3]);
 }
 
-// ---------------------------------------------------------------------------
-// Effective Maxwellian parameters (Sec. 2.1, remark on exact conservation),
-// run by one full warp.  D(p) = discrete moments of Phi(p) is evaluated with
-// the separable 1D sums S_k = sum_j c_j^k exp(-(c_j - u)^2/theta):
-//   n_d = n (pi theta)^(-d/2) dv Sx0 Sy0,  ux_d = Sx1/Sx0,  uy_d = Sy1/Sy0,
-//   theta_d = (2/3) (Sx2/Sx0 + Sy2/Sy0 + kappa - ux_d^2 - uy_d^2),
-// kappa = theta (dim 1) or theta/2 (dim 2) being the h-part per unit density.
-// Iteration p <- p + (q - D(p)); returns iterations used or -1.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void sep_sums(const double* c, int n, double u, double inv_th,
-                                         double& s0, double& s1, double& s2) {
-  const int lane = threadIdx.x & 31;
-  s0 = s1 = s2 = 0.0;
-  for (int j = lane; j < n; j += 32) {
-    const double cj = c[j];
-    const double d = cj - u;
-    const double e = exp(-(d * d) * inv_th);
-    s0 += e;
-    s1 = fma(cj, e, s1);
-    s2 = fma(cj * cj, e, s2);
-  }
-}
-
-__device__ inline int effective_params_warp(const Params& P, const double* cx, const double* cy,
-                                            const double q[4], double p[4]) {
-  const int lane = threadIdx.x & 31;
-  const double vs = sqrt(q[3]);
-  for (int k = 0; k < 4; ++k) p[k] = q[k];
-  double r = 0.0;
-  int it;
-  for (it = 1; it <= kEffMaxIt; ++it) {
-    const double inv_th = 1.0 / p[3];
-    double v[8];
-    sep_sums(cx, P.nvx, p[1], inv_th, v[0], v[1], v[2]);
-    if (P.dim == 2) {
-      sep_sums(cy, P.nvy, p[2], inv_th, v[3], v[4], v[5]);
-    } else {
-      v[3] = (lane == 0) ? 1.0 : 0.0;
-      v[4] = v[5] = 0.0;
-    }
-    v[6] = v[7] = 0.0;
-    const double x = warp_reduce8(v);
-    double S[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) S[k] = __shfl_sync(0xffffffffu, x, 4 * k);
-    const double pref = (P.dim == 1) ? p[0] / sqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
-    const double kappa = (P.dim == 1) ? p[3] : 0.5 * p[3];
-    double d[4];
-    d[0] = pref * P.dv * S[0] * S[3];
-    d[1] = S[1] / S[0];
-    d[2] = (P.dim == 2) ? S[4] / S[3] : 0.0;
-    d[3] = (2.0 / 3.0) * (S[2] / S[0] + S[5] / S[3] + kappa - (d[1] * d[1] + d[2] * d[2]));
-    double delta[4];
-    for (int k = 0; k < 4; ++k) delta[k] = q[k] - d[k];
-    for (int k = 0; k < 4; ++k) p[k] += delta[k];
-    r = fabs(delta[0]) / q[0];
-    r = fmax(r, fabs(delta[1]) / vs);
-    r = fmax(r, fabs(delta[2]) / vs);
-    r = fmax(r, fabs(delta[3]) / q[3]);
-    if (!(p[0] > 0.0) || !(p[3] > 0.0) || !isfinite(r)) return -1;
-    if (r < kEffTol) return it;
-  }
-  return (r < kEffFail) ? kEffMaxIt : -1;
-}
-
-// Final Maxwellian factors of Phi(p) scaled by the relaxation weight a:
-//   phx[jx] = a n (pi theta)^(-d/2) e^{-(cx-ux)^2/theta},
-//   phy[jy] = e^{-(cy-uy)^2/theta}  (dim 2),
-// so that a Phi_g = phx[jx] phy[jy] and a Phi_h = kappa a Phi_g.  One warp.
-__device__ __forceinline__ void maxwell_factors_warp(const Params& P, const double* cx,
-                                                     const double* cy, const double p[4], double a,
-                                                     double* phx, double* phy) {
-  const int lane = threadIdx.x & 31;
-  const double pref = (P.dim == 1) ? p[0] / sqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
-  const double ap = a * pref;
-  const double inv_th = 1.0 / p[3];
-  for (int j = lane; j < P.nvx; j += 32) {
-    const double d = cx[j] - p[1];
-    phx[j] = ap * exp(-(d * d) * inv_th);
-  }
-  if (P.dim == 2) {
-    for (int j = lane; j < P.nvy; j += 32) {
-      const double d = cy[j] - p[2];
-      phy[j] = exp(-(d * d) * inv_th);
-    }
-  }
-}
-
 // Boundary value (g, h) just outside `face` at velocity j: the inflow
 // Maxwellian, n_W times the unit wall Maxwellian, or the mirror image of the
 // wall-adjacent cell's own state `fc` (specular).

@@ -21,10 +21,15 @@ enum { ERR_MOMENT = 1, ERR_EFFECTIVE = 2 };
 constexpr double kEffTol = 1e-13;
 constexpr int kEffMaxIt = 20;
 constexpr double kEffFail = 1e-9;
+// The GPU evaluates the Gaussians once per cell and moves them to a nearby
+// parameter point to first order; beyond this relative distance it
+// re-evaluates (the neglected second-order terms stay below 1e-15).
+constexpr double kLinMax = 1e-8;
 
 // Scalar description of one problem, passed by value to every kernel.
 struct Params {
   int dim, nx, ny, nvx, nvy, nv;
+  int tile;  // spatial cells per CTA of the step kernel (1, 2, 4 or 8)
   int conservative, relax_exact;
   int bc_kind[kFaces];
   double dt, dx, dy, dcx, dcy, dv;
@@ -40,6 +45,8 @@ struct Tables {
   const double4_32a* coef;    // [nv] (a0, ax, ay, |c|^2): streaming weights, 2D
                           //      (w_near, w_far, 0, c_x^2): 1D
   const int* shift;       // [nv] 1D integer Courant shift [C] (0 in 2D)
+  const double2* cxy;     // [nv] (c_x, c_y) per velocity
+  const int* vinfo;       // [nv] jx | jy << 12 | (sgn c_x + 1) << 24 | (sgn c_y + 1) << 26
   const double2* ghost;   // [kFaces][nv] inflow Maxwellian, or the unit-density
                           //   wall Maxwellian for diffuse faces
   const double* emitted;  // [kFaces] sum_{c_n>0} c_n G_W(n=1) dv (diffuse)
@@ -49,7 +56,10 @@ struct Tables {
 cudaError_t launch_step_f64(const Params& P, const Tables& T, const double2* fin, double2* fout,
                             double4_32a* mom, int* err, cudaStream_t stream);
 cudaError_t launch_build_tables(const Params& P, double* cx, double* cy, double4_32a* coef, int* shift,
-                                double2* ghost, double* emitted, cudaStream_t stream);
+                                double2* cxy, int* vinfo, double2* ghost, double* emitted,
+                                cudaStream_t stream);
+size_t step_f64_smem_bytes(const Params& P, int tile);
+cudaError_t prepare_step_f64(const Params& P);
 cudaError_t launch_init_step(const Params& P, double2* f, double x_split, const double left[4],
                              const double right[4], cudaStream_t stream);
 cudaError_t launch_init_uniform(const Params& P, double2* f, const double state[4],

@@ -1,223 +1,442 @@
 // bgk_step.cu - the fused FP64 BGK phase-space step.
 //
-// One CTA owns one spatial cell and all of its velocities (threads stride
-// over the velocity index v = jy*nvx + jx, 16-byte (g, h) pairs).  Per step
-// and cell the CTA
-//   A0  computes the diffuse-wall densities n_W of the faces the cell
-//       touches from its own f^n (zero net mass flux, below Eq. bc_cavity);
-//   A1  streams: f~ = a0 f + ax f_(upwind x) + ay f_(upwind y) (2D unsplit
-//       donor cell), or f~ = (1-|r|) f_(i-[C]) + |r| f_(i-[C]-sgn C) (1D,
-//       Eq. upwind after the integer shift of Eq. exact), neighbours read
-//       from L2 and boundary values from the ghost tables;
-//   A2  reduces the moments of f~ (Eq. macroscopic) in FP64;
-//   A3  forms nu = n theta^(1-omega) and the (effective) Maxwellian
-//       parameters in one warp, writing separable factors to shared memory;
-//   A4  relaxes in registers, f^{n+1} = b f~ + a Phi (Eq. relaxation:
-//       b = e^{-nu dt}, a = 1 - b; Euler: a = nu dt, b = 1 - a), and stores.
-// f^n is read once from HBM and f^{n+1} written once; neighbour re-reads of
-// the same f^n hit L2 because CTAs run in raster order.
-#include <cstdio>
-
+// A CTA owns G spatial cells, one warp per cell; lanes stride over the
+// velocity index v = jy*nvx + jx with 16-byte (g, h) pairs.  Per step:
+//   phase 1 (each warp, its cell)
+//     A0  diffuse-wall densities n_W of the faces the cell touches, from the
+//         cell's own f^n (zero net mass flux, below Eq. bc_cavity);
+//     A1  streaming: f~ = a0 f + ax f_(upwind x) + ay f_(upwind y) (2D
+//         unsplit donor cell), or f~ = (1-|r|) f_(i-[C]) + |r| f_(i-[C]-sgn C)
+//         (1D, Eq. upwind after the integer shift of Eq. exact); upwind
+//         neighbours come from L2, boundary values from the ghost tables;
+//         f~ is staged in shared memory;
+//     A2  FP64 velocity sums of f~ for Eq. (macroscopic), one warp reduction;
+//   phase 2 (warp 0, the G cells in lanes)
+//     A3  moments, nu = n theta^(1-omega), relaxation weights and the
+//         effective Maxwellian parameters (one set of exponentials per cell,
+//         linearised updates), separable factors written to shared memory;
+//   phase 3 (each warp, its cell)
+//     A4  f^{n+1} = b f~ + a Phi (Eq. relaxation: b = e^{-nu dt}, a = 1 - b;
+//         Euler: a = nu dt, b = 1 - a), stored to HBM.
+// The FP64 pipe of sm_103 charges every warp instruction in full whatever the
+// number of active lanes, so the per-cell scalar work of phase 2 runs with
+// cells in lanes (G cells per instruction) and sign tests use integer tables.
 #include "bgk_device.cuh"
 
 namespace bgk {
 
-template <int DIM, int BLOCK, int NPT>
-__global__ void __launch_bounds__(BLOCK)
-    step_f64_kernel(const double2* __restrict__ fin, double2* __restrict__ fout,
-                    double4_32a* __restrict__ mom, const Params P, const Tables T, int* __restrict__ err) {
-  extern __shared__ double sh_dyn[];  // phx[nvx], phy[nvy]
-  __shared__ double red[4 * (BLOCK / 32)];
-  __shared__ double tot[4];
-  __shared__ double sc[8];  // 0..3: n_W per face; 4: b; 5: kappa; 6: ok
-  double* phx = sh_dyn;
-  double* phy = sh_dyn + P.nvx;
+namespace {
 
-  const int cell = blockIdx.x;
-  const int tid = threadIdx.x;
-  const int nx = P.nx, nv = P.nv;
+__device__ __forceinline__ int vi_jx(int vi) { return vi & 0xfff; }
+__device__ __forceinline__ int vi_jy(int vi) { return (vi >> 12) & 0xfff; }
+__device__ __forceinline__ int vi_sx(int vi) { return ((vi >> 24) & 3) - 1; }
+__device__ __forceinline__ int vi_sy(int vi) { return ((vi >> 26) & 3) - 1; }
+
+// Boundary value at velocity j (components jx, jy) for a face of the cell
+// whose state starts at fc.
+__device__ __forceinline__ double2 ghost_at(const Params& P, const Tables& T, int face, int j, int jx,
+                                            int jy, double nw, const double2* __restrict__ fc) {
+  const int kind = P.bc_kind[face];
+  if (kind == BC_SPECULAR) {
+    const int jr = (face == XLO || face == XHI) ? jy * P.nvx + (P.nvx - 1 - jx)
+                                                : (P.nvy - 1 - jy) * P.nvx + jx;
+    return fc[jr];
+  }
+  const double2 gv = T.ghost[face * P.nv + j];
+  if (kind == BC_DIFFUSE) return make_double2(nw * gv.x, nw * gv.y);
+  return gv;
+}
+
+// ---- phase 1 ---------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void stream_cell(const Params& P, const Tables& T,
+                                            const double2* __restrict__ fin, int cell,
+                                            double2* __restrict__ tile, double* __restrict__ sums) {
+  const int lane = threadIdx.x & 31;
+  const int nv = P.nv, nx = P.nx;
   const int ix = cell % nx, iy = cell / nx;
   const double2* __restrict__ fc = fin + (size_t)cell * nv;
+  const bool bxlo = ix == 0, bxhi = ix == nx - 1;
+  const bool bylo = DIM == 2 && iy == 0, byhi = DIM == 2 && iy == P.ny - 1;
 
-  double2 own[NPT];
-#pragma unroll
-  for (int k = 0; k < NPT; ++k) {
-    const int j = tid + k * BLOCK;
-    own[k] = (j < nv) ? __ldg(fc + j) : make_double2(0.0, 0.0);
-  }
-
-  // ---- A0: diffuse-wall densities for the faces this cell touches ---------
+  // A0: n_W for each diffuse face this cell touches (warp-uniform branch)
   unsigned diff = 0;
-  if (ix == 0 && P.bc_kind[XLO] == BC_DIFFUSE) diff |= 1u;
-  if (ix == nx - 1 && P.bc_kind[XHI] == BC_DIFFUSE) diff |= 2u;
-  if (DIM == 2) {
-    if (iy == 0 && P.bc_kind[YLO] == BC_DIFFUSE) diff |= 4u;
-    if (iy == P.ny - 1 && P.bc_kind[YHI] == BC_DIFFUSE) diff |= 8u;
-  }
-  if (diff) {  // uniform over the CTA
+  if (bxlo && P.bc_kind[XLO] == BC_DIFFUSE) diff |= 1u;
+  if (bxhi && P.bc_kind[XHI] == BC_DIFFUSE) diff |= 2u;
+  if (bylo && P.bc_kind[YLO] == BC_DIFFUSE) diff |= 4u;
+  if (byhi && P.bc_kind[YHI] == BC_DIFFUSE) diff |= 8u;
+  double nw[4] = {0.0, 0.0, 0.0, 0.0};
+  if (diff) {
     double inc[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      const int j = tid + k * BLOCK;
-      if (j < nv) {
-        const double cx = T.cx[DIM == 2 ? j % P.nvx : j];
-        const double g = own[k].x;
-        if (cx < 0.0) inc[0] = fma(-cx, g, inc[0]);
-        if (cx > 0.0) inc[1] = fma(cx, g, inc[1]);
-        if (DIM == 2) {
-          const double cy = T.cy[j / P.nvx];
-          if (cy < 0.0) inc[2] = fma(-cy, g, inc[2]);
-          if (cy > 0.0) inc[3] = fma(cy, g, inc[3]);
-        }
-      }
+    for (int j = lane; j < nv; j += 32) {
+      const int vi = T.vinfo[j];
+      const double2 cxy = T.cxy[j];
+      const double g = fc[j].x;
+      const int sx = vi_sx(vi), sy = vi_sy(vi);
+      if (sx < 0) inc[0] = fma(-cxy.x, g, inc[0]);
+      if (sx > 0) inc[1] = fma(cxy.x, g, inc[1]);
+      if (sy < 0) inc[2] = fma(-cxy.y, g, inc[2]);
+      if (sy > 0) inc[3] = fma(cxy.y, g, inc[3]);
     }
-    block_reduce4<BLOCK>(inc[0], inc[1], inc[2], inc[3], red, tot);
-    if (tid < 4) sc[tid] = (diff >> tid & 1u) ? tot[tid] * P.dv / T.emitted[tid] : 0.0;
-    __syncthreads();
+    const double w = warp_reduce4(inc[0], inc[1], inc[2], inc[3]);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const double tot = __shfl_sync(0xffffffffu, w, 8 * f);
+      nw[f] = (diff >> f & 1u) ? tot * P.dv / T.emitted[f] : 0.0;
+    }
   }
 
-  // ---- A1: free streaming ----------------------------------------------
-  double2 ft[NPT];
   double s0 = 0.0, sx = 0.0, sy = 0.0, se = 0.0;
-#pragma unroll
-  for (int k = 0; k < NPT; ++k) {
-    const int j = tid + k * BLOCK;
-    ft[k] = make_double2(0.0, 0.0);
-    if (j < nv) {
+  if (DIM == 2) {
+    const ptrdiff_t row = (ptrdiff_t)nx * nv;
+    if (!(bxlo || bxhi || bylo || byhi)) {
+      // interior cell: every upwind neighbour is a cell of the grid
+#pragma unroll 4
+      for (int j = lane; j < nv; j += 32) {
+        const int vi = T.vinfo[j];
+        const double2 f0 = fc[j];
+        const double2 fx = fc[j - vi_sx(vi) * nv];
+        const double2 fy = fc[j - vi_sy(vi) * row];
+        const double4_32a co = T.coef[j];
+        const double2 cxy = T.cxy[j];
+        double2 ft;
+        ft.x = fma(co.z, fy.x, fma(co.y, fx.x, co.x * f0.x));
+        ft.y = fma(co.z, fy.y, fma(co.y, fx.y, co.x * f0.y));
+        tile[j] = ft;
+        s0 += ft.x;
+        sx = fma(cxy.x, ft.x, sx);
+        sy = fma(cxy.y, ft.x, sy);
+        se = fma(co.w, ft.x, se) + ft.y;
+      }
+    } else {
+      for (int j = lane; j < nv; j += 32) {
+        const int vi = T.vinfo[j];
+        const int jx = vi_jx(vi), jy = vi_jy(vi), sgx = vi_sx(vi), sgy = vi_sy(vi);
+        const double2 f0 = fc[j];
+        double2 fx = f0, fy = f0;
+        if (sgx > 0) fx = bxlo ? ghost_at(P, T, XLO, j, jx, jy, nw[XLO], fc) : fc[j - nv];
+        else if (sgx < 0) fx = bxhi ? ghost_at(P, T, XHI, j, jx, jy, nw[XHI], fc) : fc[j + nv];
+        if (sgy > 0) fy = bylo ? ghost_at(P, T, YLO, j, jx, jy, nw[YLO], fc) : fc[j - row];
+        else if (sgy < 0) fy = byhi ? ghost_at(P, T, YHI, j, jx, jy, nw[YHI], fc) : fc[j + row];
+        const double4_32a co = T.coef[j];
+        const double2 cxy = T.cxy[j];
+        double2 ft;
+        ft.x = fma(co.z, fy.x, fma(co.y, fx.x, co.x * f0.x));
+        ft.y = fma(co.z, fy.y, fma(co.y, fx.y, co.x * f0.y));
+        tile[j] = ft;
+        s0 += ft.x;
+        sx = fma(cxy.x, ft.x, sx);
+        sy = fma(cxy.y, ft.x, sy);
+        se = fma(co.w, ft.x, se) + ft.y;
+      }
+    }
+  } else {
+    for (int j = lane; j < nv; j += 32) {
+      const int vi = T.vinfo[j];
+      const int sgx = vi_sx(vi);
+      const int s = T.shift[j];
+      const int i1 = ix - s, i2 = ix - s - sgx;
+      double2 f1, f2;
+      if (i1 < 0) f1 = ghost_at(P, T, XLO, j, j, 0, nw[XLO], fc);
+      else if (i1 >= nx) f1 = ghost_at(P, T, XHI, j, j, 0, nw[XHI], fc);
+      else f1 = fin[(size_t)i1 * nv + j];
+      if (i2 < 0) f2 = ghost_at(P, T, XLO, j, j, 0, nw[XLO], fc);
+      else if (i2 >= nx) f2 = ghost_at(P, T, XHI, j, j, 0, nw[XHI], fc);
+      else f2 = fin[(size_t)i2 * nv + j];
       const double4_32a co = T.coef[j];
-      if (DIM == 2) {
-        const int jx = j % P.nvx, jy = j / P.nvx;
-        const double cx = T.cx[jx], cy = T.cy[jy];
-        double2 fx = own[k], fy = own[k];
-        if (cx > 0.0) {
-          fx = (ix > 0) ? fin[(size_t)(cell - 1) * nv + j] : ghost_value(P, T, XLO, j, sc[XLO], fc);
-        } else if (cx < 0.0) {
-          fx = (ix < nx - 1) ? fin[(size_t)(cell + 1) * nv + j] : ghost_value(P, T, XHI, j, sc[XHI], fc);
-        }
-        if (cy > 0.0) {
-          fy = (iy > 0) ? fin[(size_t)(cell - nx) * nv + j] : ghost_value(P, T, YLO, j, sc[YLO], fc);
-        } else if (cy < 0.0) {
-          fy = (iy < P.ny - 1) ? fin[(size_t)(cell + nx) * nv + j] : ghost_value(P, T, YHI, j, sc[YHI], fc);
-        }
-        ft[k].x = fma(co.z, fy.x, fma(co.y, fx.x, co.x * own[k].x));
-        ft[k].y = fma(co.z, fy.y, fma(co.y, fx.y, co.x * own[k].y));
-        // ---- A2 (partial): velocity sums of f~ -----------------------------
-        s0 += ft[k].x;
-        sx = fma(cx, ft[k].x, sx);
-        sy = fma(cy, ft[k].x, sy);
-        se = fma(co.w, ft[k].x, se) + ft[k].y;
-      } else {
-        const double cx = T.cx[j];
-        const int s = T.shift[j];
-        const int up = cx > 0.0 ? 1 : -1;
-        const int i1 = ix - s, i2 = ix - s - up;
-        double2 f1, f2;
-        if (s == 0) f1 = own[k];
-        else if (i1 < 0) f1 = ghost_value(P, T, XLO, j, sc[XLO], fc);
-        else if (i1 >= nx) f1 = ghost_value(P, T, XHI, j, sc[XHI], fc);
-        else f1 = fin[(size_t)i1 * nv + j];
-        if (i2 < 0) f2 = ghost_value(P, T, XLO, j, sc[XLO], fc);
-        else if (i2 >= nx) f2 = ghost_value(P, T, XHI, j, sc[XHI], fc);
-        else f2 = fin[(size_t)i2 * nv + j];
-        ft[k].x = fma(co.y, f2.x, co.x * f1.x);
-        ft[k].y = fma(co.y, f2.y, co.x * f1.y);
-        s0 += ft[k].x;
-        sx = fma(cx, ft[k].x, sx);
-        se = fma(co.w, ft[k].x, se) + ft[k].y;
-      }
+      const double cx = T.cxy[j].x;
+      double2 ft;
+      ft.x = fma(co.y, f2.x, co.x * f1.x);
+      ft.y = fma(co.y, f2.y, co.x * f1.y);
+      tile[j] = ft;
+      s0 += ft.x;
+      sx = fma(cx, ft.x, sx);
+      se = fma(co.w, ft.x, se) + ft.y;
     }
   }
+  const double w = warp_reduce4(s0, sx, sy, se);
+  if ((lane & 7) == 0) sums[lane >> 3] = w;
+}
 
-  // ---- A2: block reduction of the moments --------------------------------
-  block_reduce4<BLOCK>(s0, sx, sy, se, red, tot);
-
-  // ---- A3: nu and the Maxwellian, one warp --------------------------------
-  if (tid < 32) {
-    double q[4];
-    moments_from_sums(tot[0], tot[1], tot[2], tot[3], P.dv, q);
-    bool ok = moments_ok(q);
-    double p[4] = {q[0], q[1], q[2], q[3]};
-    double a = 0.0, b = 1.0;
-    if (ok) {
-      const double nu = q[0] * pow(q[3], 1.0 - P.omega);
-      if (P.relax_exact) {
-        b = exp(-nu * P.dt);
-        a = 1.0 - b;
-      } else {
-        a = P.dt * nu;
-        b = 1.0 - a;
-      }
-      if (P.conservative && effective_params_warp(P, T.cx, T.cy, q, p) < 0) {
-        ok = false;
-        if (tid == 0) atomicOr(err, ERR_EFFECTIVE);
-      }
-    } else if (tid == 0) {
-      atomicOr(err, ERR_MOMENT);
-    }
-    if (ok) maxwell_factors_warp(P, T.cx, T.cy, p, a, phx, phy);
-    if (tid == 0) {
-      mom[cell] = make_double4_32a(q[0], q[1], q[2], q[3]);
-      sc[4] = b;
-      sc[5] = (DIM == 1) ? p[3] : 0.5 * p[3];
-      sc[6] = ok ? 1.0 : 0.0;
+// ---- phase 2 ---------------------------------------------------------------
+// Exponentials e_j = exp(-(c_j - u)^2 / theta) of one axis for one cell,
+// lanes sub, sub + L, ... of the cell's group; stores them when `store`;
+// returns the group's central sums M_m = sum d^m e, d = c_j - u, m = 0..4.
+template <int L>
+__device__ __forceinline__ void axis_sums(const double* __restrict__ c, int n, double u, double inv_th,
+                                          int sub, bool store, double* __restrict__ out, bool want,
+                                          double M[5]) {
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, m4 = 0.0;
+  for (int j = sub; j < n; j += L) {
+    const double d = c[j] - u;
+    const double e = exp(-(d * d) * inv_th);
+    if (store) out[j] = e;
+    if (want) {
+      double t = e;
+      m0 += t;
+      t *= d;
+      m1 += t;
+      t *= d;
+      m2 += t;
+      t *= d;
+      m3 += t;
+      t *= d;
+      m4 += t;
     }
   }
-  __syncthreads();
-
-  // ---- A4: relaxation and store --------------------------------------------
-  const double b = sc[4], kappa = sc[5];
-  const bool ok = sc[6] != 0.0;
-  double2* __restrict__ fo = fout + (size_t)cell * nv;
+  if (want) {
 #pragma unroll
-  for (int k = 0; k < NPT; ++k) {
-    const int j = tid + k * BLOCK;
-    if (j < nv) {
-      double2 r = ft[k];
-      if (ok) {
-        const double aphi = (DIM == 2) ? phx[j % P.nvx] * phy[j / P.nvx] : phx[j];
-        r.x = fma(b, ft[k].x, aphi);
-        r.y = fma(b, ft[k].y, kappa * aphi);
-      }
-      fo[j] = r;
+    for (int s = 1; s < L; s <<= 1) {
+      m0 += __shfl_xor_sync(0xffffffffu, m0, s);
+      m1 += __shfl_xor_sync(0xffffffffu, m1, s);
+      m2 += __shfl_xor_sync(0xffffffffu, m2, s);
+      m3 += __shfl_xor_sync(0xffffffffu, m3, s);
+      m4 += __shfl_xor_sync(0xffffffffu, m4, s);
     }
+  }
+  M[0] = m0;
+  M[1] = m1;
+  M[2] = m2;
+  M[3] = m3;
+  M[4] = m4;
+}
+
+// Sums of the Gaussian moved from base (u0, th0) to (u0 + du, th0 + dth), to
+// first order: e' = e (1 + d (w1 + d w2)), w1 = 2 du / th0, w2 = dth / th0^2.
+__device__ __forceinline__ void shifted(const double M[5], double w1, double w2, double out[3]) {
+#pragma unroll
+  for (int m = 0; m < 3; ++m) out[m] = M[m] + w1 * M[m + 1] + w2 * M[m + 2];
+}
+
+template <int DIM, int G>
+__device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, const double (*sums)[4],
+                                 double* __restrict__ phx, double* __restrict__ phy, double* sb,
+                                 double* sk, int* sok, double4_32a* __restrict__ mom, int* __restrict__ err) {
+  constexpr int L = 32 / G;
+  const int lane = threadIdx.x & 31, c = lane / L, sub = lane % L;
+  const int cell = cell0 + c;
+  const bool live = cell < P.nx * P.ny;
+  double qm[4] = {1.0, 0.0, 0.0, 1.0};  // moments of f~ (Eq. macroscopic)
+  if (live) moments_from_sums(sums[c][0], sums[c][1], sums[c][2], sums[c][3], P.dv, qm);
+  bool ok = live && moments_ok(qm);
+  // a failed cell keeps its lanes busy on a harmless stand-in state
+  const double q[4] = {ok ? qm[0] : 1.0, ok ? qm[1] : 0.0, ok ? qm[2] : 0.0, ok ? qm[3] : 1.0};
+  // relaxation weights from nu = n theta^(1-omega)
+  double a = 0.0, b = 1.0;
+  {
+    const double nu = q[0] * (P.omega == 0.5 ? sqrt(q[3]) : pow(q[3], 1.0 - P.omega));
+    if (P.relax_exact) {
+      b = exp(-nu * P.dt);
+      a = 1.0 - b;
+    } else {
+      a = P.dt * nu;
+      b = 1.0 - a;
+    }
+  }
+  double* px = phx + c * P.nvx;
+  double* py = phy + c * P.nvy;
+  const bool cons = P.conservative != 0;
+  double base[4] = {q[0], q[1], q[2], q[3]};
+  double p[4] = {q[0], q[1], q[2], q[3]};
+  double Mx[5], My[5] = {1.0, 0.0, 0.0, 0.0, 0.0};
+  bool conv = !(cons && ok), fail = false, reeval = false;
+  int it = 0;
+  const double vs = sqrt(q[3]);
+  for (int round = 0; round <= kEffMaxIt; ++round) {
+    const bool need = round == 0 || reeval;
+    if (!__any_sync(0xffffffffu, need)) break;
+    {
+      const double inv_th = 1.0 / base[3];
+      double Mt[5];
+      axis_sums<L>(T.cx, P.nvx, base[1], inv_th, sub, need, px, cons, Mt);
+      if (need)
+        for (int m = 0; m < 5; ++m) Mx[m] = Mt[m];
+      if (DIM == 2) {
+        axis_sums<L>(T.cy, P.nvy, base[2], inv_th, sub, need, py, cons, Mt);
+        if (need)
+          for (int m = 0; m < 5; ++m) My[m] = Mt[m];
+      }
+    }
+    reeval = false;
+    // A3: effective parameters, p <- p + (q - D(p)), D linearised about base
+    while (!conv && !fail && !reeval) {
+      ++it;
+      const double ith = 1.0 / base[3];
+      const double w2 = (p[3] - base[3]) * ith * ith;
+      double Sx[3], Sy[3] = {1.0, 0.0, 0.0};
+      shifted(Mx, 2.0 * (p[1] - base[1]) * ith, w2, Sx);
+      if (DIM == 2) shifted(My, 2.0 * (p[2] - base[2]) * ith, w2, Sy);
+      const double pref = (DIM == 1) ? p[0] / sqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
+      const double rx = 1.0 / Sx[0], ry = 1.0 / Sy[0];
+      const double mux = Sx[1] * rx, muy = Sy[1] * ry;
+      double d[4];
+      d[0] = pref * P.dv * Sx[0] * Sy[0];
+      d[1] = base[1] + mux;
+      d[2] = (DIM == 2) ? base[2] + muy : 0.0;
+      const double kappa = (DIM == 1) ? p[3] : 0.5 * p[3];
+      const double var = (Sx[2] * rx - mux * mux) + ((DIM == 2) ? (Sy[2] * ry - muy * muy) : 0.0);
+      d[3] = (2.0 / 3.0) * (var + kappa);
+      double r = 0.0;
+      for (int k = 0; k < 4; ++k) {
+        const double delta = q[k] - d[k];
+        p[k] += delta;
+        const double scale = (k == 0) ? q[0] : (k == 3) ? q[3] : vs;
+        r = fmax(r, fabs(delta) / scale);
+      }
+      if (!(p[0] > 0.0) || !(p[3] > 0.0) || !isfinite(r)) {
+        fail = true;
+      } else if (r < kEffTol) {
+        conv = true;
+      } else if (it >= kEffMaxIt) {
+        if (r < kEffFail) conv = true;
+        else fail = true;
+      }
+      if (!fail) {
+        const double drift = fmax(fmax(fabs(p[0] - base[0]) / base[0], fabs(p[3] - base[3]) / base[3]),
+                                  fmax(fabs(p[1] - base[1]), fabs(p[2] - base[2])) / sqrt(base[3]));
+        if (drift > kLinMax) {
+          for (int k = 0; k < 4; ++k) base[k] = p[k];
+          reeval = true;
+        }
+      }
+    }
+  }
+  if (fail) ok = false;
+  if (ok) {
+    // A4 factors: a Phi_g = px[jx] py[jy], linearised from base to p
+    const double ith = 1.0 / base[3];
+    const double w2 = (p[3] - base[3]) * ith * ith;
+    const double w1x = 2.0 * (p[1] - base[1]) * ith, w1y = 2.0 * (p[2] - base[2]) * ith;
+    const double pref = (DIM == 1) ? p[0] / sqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
+    const double ap = a * pref;
+    for (int j = sub; j < P.nvx; j += L) {
+      const double d = T.cx[j] - base[1];
+      px[j] = ap * (px[j] * fma(d, fma(d, w2, w1x), 1.0));
+    }
+    if (DIM == 2) {
+      for (int j = sub; j < P.nvy; j += L) {
+        const double d = T.cy[j] - base[2];
+        py[j] = py[j] * fma(d, fma(d, w2, w1y), 1.0);
+      }
+    }
+  }
+  if (sub == 0 && c < G) {
+    sb[c] = b;
+    sk[c] = (DIM == 1) ? p[3] : 0.5 * p[3];
+    sok[c] = ok ? 1 : 0;
+    if (live) {
+      mom[cell] = make_double4_32a(qm[0], qm[1], qm[2], qm[3]);
+      if (!ok) atomicOr(err, fail ? ERR_EFFECTIVE : ERR_MOMENT);
+    }
+  }
+}
+
+}  // namespace
+
+template <int DIM, int G>
+__global__ void __launch_bounds__(32 * G)
+    step_f64_kernel(const double2* __restrict__ fin, double2* __restrict__ fout,
+                    double4_32a* __restrict__ mom, const Params P, const Tables T, int* __restrict__ err) {
+  extern __shared__ double4_32a smem4[];
+  double2* ftile = reinterpret_cast<double2*>(smem4);
+  double* phx = reinterpret_cast<double*>(ftile + (size_t)G * P.nv);
+  double* phy = phx + G * P.nvx;
+  __shared__ double s_sum[G][4];
+  __shared__ double s_b[G], s_k[G];
+  __shared__ int s_ok[G];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nv = P.nv;
+  const int cell = blockIdx.x * G + warp;
+  const bool live = cell < P.nx * P.ny;
+  double2* tile = ftile + (size_t)warp * nv;
+
+  if (live) stream_cell<DIM>(P, T, fin, cell, tile, s_sum[warp]);
+  __syncthreads();
+  if (warp == 0) maxwellian_cells<DIM, G>(P, T, blockIdx.x * G, s_sum, phx, phy, s_b, s_k, s_ok, mom, err);
+  __syncthreads();
+  if (!live) return;
+
+  const double b = s_b[warp], kappa = s_k[warp];
+  const bool ok = s_ok[warp] != 0;
+  const double* px = phx + warp * P.nvx;
+  const double* py = phy + warp * P.nvy;
+  double2* __restrict__ fo = fout + (size_t)cell * nv;
+#pragma unroll 4
+  for (int j = lane; j < nv; j += 32) {
+    const double2 ft = tile[j];
+    double2 r = ft;
+    if (ok) {
+      double aphi;
+      if (DIM == 2) {
+        const int vi = T.vinfo[j];
+        aphi = px[vi_jx(vi)] * py[vi_jy(vi)];
+      } else {
+        aphi = px[j];
+      }
+      r.x = fma(b, ft.x, aphi);
+      r.y = fma(b, ft.y, kappa * aphi);
+    }
+    fo[j] = r;
   }
 }
 
 namespace {
 
-template <int DIM, int BLOCK, int NPT>
-cudaError_t launch_t(const Params& P, const Tables& T, const double2* fin, double2* fout,
+size_t step_smem(const Params& P, int G) {
+  return sizeof(double2) * (size_t)G * P.nv + sizeof(double) * (size_t)G * (P.nvx + P.nvy);
+}
+
+template <int DIM, int G>
+cudaError_t launch_g(const Params& P, const Tables& T, const double2* fin, double2* fout,
                      double4_32a* mom, int* err, cudaStream_t stream) {
-  const size_t shmem = sizeof(double) * (P.nvx + (DIM == 2 ? P.nvy : 0));
-  step_f64_kernel<DIM, BLOCK, NPT><<<P.nx * P.ny, BLOCK, shmem, stream>>>(fin, fout, mom, P, T, err);
+  const int ncell = P.nx * P.ny;
+  const unsigned grid = (unsigned)((ncell + G - 1) / G);
+  step_f64_kernel<DIM, G><<<grid, 32 * G, step_smem(P, G), stream>>>(fin, fout, mom, P, T, err);
   return cudaGetLastError();
 }
 
-template <int DIM, int BLOCK>
-cudaError_t dispatch_npt(const Params& P, const Tables& T, const double2* fin, double2* fout,
-                         double4_32a* mom, int* err, cudaStream_t stream) {
-  const int need = (P.nv + BLOCK - 1) / BLOCK;
-  if (need <= 1) return launch_t<DIM, BLOCK, 1>(P, T, fin, fout, mom, err, stream);
-  if (need <= 2) return launch_t<DIM, BLOCK, 2>(P, T, fin, fout, mom, err, stream);
-  if (need <= 3) return launch_t<DIM, BLOCK, 3>(P, T, fin, fout, mom, err, stream);
-  if (need <= 4) return launch_t<DIM, BLOCK, 4>(P, T, fin, fout, mom, err, stream);
-  if (need <= 6) return launch_t<DIM, BLOCK, 6>(P, T, fin, fout, mom, err, stream);
-  if (need <= 8) return launch_t<DIM, BLOCK, 8>(P, T, fin, fout, mom, err, stream);
-  if (need <= 9) return launch_t<DIM, BLOCK, 9>(P, T, fin, fout, mom, err, stream);
-  if (need <= 12) return launch_t<DIM, BLOCK, 12>(P, T, fin, fout, mom, err, stream);
-  if (need <= 16) return launch_t<DIM, BLOCK, 16>(P, T, fin, fout, mom, err, stream);
+template <int DIM, int G>
+cudaError_t prepare_g(const Params& P) {
+  return cudaFuncSetAttribute(step_f64_kernel<DIM, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)step_smem(P, G));
+}
+
+template <int DIM>
+cudaError_t dispatch(const Params& P, const Tables& T, const double2* fin, double2* fout,
+                     double4_32a* mom, int* err, cudaStream_t stream) {
+  switch (P.tile) {
+    case 1: return launch_g<DIM, 1>(P, T, fin, fout, mom, err, stream);
+    case 2: return launch_g<DIM, 2>(P, T, fin, fout, mom, err, stream);
+    case 4: return launch_g<DIM, 4>(P, T, fin, fout, mom, err, stream);
+    case 8: return launch_g<DIM, 8>(P, T, fin, fout, mom, err, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int DIM>
+cudaError_t prepare_dim(const Params& P) {
+  switch (P.tile) {
+    case 1: return prepare_g<DIM, 1>(P);
+    case 2: return prepare_g<DIM, 2>(P);
+    case 4: return prepare_g<DIM, 4>(P);
+    case 8: return prepare_g<DIM, 8>(P);
+  }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
+size_t step_f64_smem_bytes(const Params& P, int tile) { return step_smem(P, tile); }
+
+cudaError_t prepare_step_f64(const Params& P) {
+  return P.dim == 1 ? prepare_dim<1>(P) : prepare_dim<2>(P);
+}
+
 cudaError_t launch_step_f64(const Params& P, const Tables& T, const double2* fin, double2* fout,
                             double4_32a* mom, int* err, cudaStream_t stream) {
-  if (P.dim == 1) {
-    if (P.nv <= 64 * 16) return dispatch_npt<1, 64>(P, T, fin, fout, mom, err, stream);
-    return dispatch_npt<1, 256>(P, T, fin, fout, mom, err, stream);
-  }
-  return dispatch_npt<2, 256>(P, T, fin, fout, mom, err, stream);
+  return P.dim == 1 ? dispatch<1>(P, T, fin, fout, mom, err, stream)
+                    : dispatch<2>(P, T, fin, fout, mom, err, stream);
 }
 
 }  // namespace bgk

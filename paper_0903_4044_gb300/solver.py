@@ -88,18 +88,18 @@ class Solver:
 
 
 def shock_config(*, mach, nx, length, nvx, vx, omega, cfl, conservative=1, relax_exact=1,
-                 precision=B.BGK_F64, stream=None, **_ignored):
+                 precision=B.BGK_F64, tile_cells=0, stream=None, **_ignored):
     """(cfg, up, down) for the Sec. 4.1 normal shock."""
     up, down = B.bgk_rankine_hugoniot(mach, GAMMA)
     bc = [(B.BGK_BC_INFLOW, *up), (B.BGK_BC_INFLOW, *down)]
     cfg = B.make_config(dim=1, nx=nx, ny=1, x0=-0.5 * length, lx=length, nvx=nvx, nvy=1, vx=vx,
                         omega=omega, cfl=cfl, conservative=conservative, relax_exact=relax_exact,
-                        precision=precision, bc=bc, stream=stream)
+                        precision=precision, tile_cells=tile_cells, bc=bc, stream=stream)
     return cfg, up, down
 
 
 def cavity_config(*, kn, lid_mach, n, nv, vbox, omega, cfl, conservative=1, relax_exact=1,
-                  precision=B.BGK_F64, wall="diffuse", stream=None, **_ignored):
+                  precision=B.BGK_F64, wall="diffuse", tile_cells=0, stream=None, **_ignored):
     """cfg for the Sec. 5.1 lid-driven cavity (lid at y = L moving along +x)."""
     side = 1.0 / kn
     uw = lid_mach * math.sqrt(GAMMA / 2.0)
@@ -108,7 +108,8 @@ def cavity_config(*, kn, lid_mach, n, nv, vbox, omega, cfl, conservative=1, rela
     lid = (kind, 1.0, uw, 0.0, 1.0)
     return B.make_config(dim=2, nx=n, ny=n, lx=side, ly=side, nvx=nv, nvy=nv, vx=vbox, vy=vbox,
                          omega=omega, cfl=cfl, conservative=conservative, relax_exact=relax_exact,
-                         precision=precision, bc=[rest, rest, rest, lid], stream=stream)
+                         precision=precision, tile_cells=tile_cells, bc=[rest, rest, rest, lid],
+                         stream=stream)
 
 
 def make_shock(w: dict, stream=None, **over) -> Solver:

@@ -345,3 +345,26 @@ def test_numeric_failure_is_reported_not_faulted():
     s.step(2)
     s.sync()
     s.close()
+
+
+@pytest.mark.parametrize("tile", [1, 2, 4, 8])
+def test_every_tile_matches_oracle(tile):
+    # The cells-per-CTA knob changes only how work is spread over lanes.
+    w = W.scaled(W.CAVITY_64, n=13, nv=24, steps=20)
+    prob0, _, _ = oracle.cavity_problem(**w)
+    xi = W.perturbation(0, prob0.ncell, prob0.nv)
+    prob, g, h = oracle.cavity_problem(**w, xi=xi)
+    s = solver.make_cavity(w, xi=xi, tile_cells=tile)
+    assert s.info.tile_cells == tile
+    s.step(20)
+    g1, h1, mom = oracle.step(prob, g, h, 20)
+    assert_state_close(s.get_state(), g1, h1, tol=1e-12)
+    assert_moments_close(s.moments(which=1), mom, vscale=0.09)
+    s.close()
+    ws = W.scaled(W.SHOCK_M2, nx=29)
+    s = solver.make_shock(ws, tile_cells=tile)
+    prob, g, h = oracle.shock_problem(**ws)
+    s.step(20)
+    g1, h1, _ = oracle.step(prob, g, h, 20)
+    assert_state_close(s.get_state(), g1, h1, tol=1e-12)
+    s.close()
