@@ -205,6 +205,38 @@ BGK_API const char* bgk_status_string(bgk_status st);
 /* BGK_ABI_VERSION of the loaded library. */
 BGK_API int bgk_abi_version(void);
 
+/* One time step with no device allocation (the paper has no counterpart:
+ * this entry point exists for callers, not for the method).
+ *
+ * Some callers cannot let a library call cudaMalloc: code that runs under a
+ * fixed device-memory budget handed out by its host framework, or code on a
+ * path where cudaMalloc's implicit device-wide synchronisation is not
+ * allowed.  For them this call advances one state by one step using only
+ * the buffers the caller passes plus a fixed 384 KiB scratch array compiled
+ * into the library (held on every GPU that loads libbgk.so until the process
+ * exits).  The scratch holds the per-velocity tables (about 120 bytes per
+ * velocity) and the error flag, which limits this call to about 3260
+ * velocities per cell (48x48 fits, 64x64 does not); larger configurations
+ * get BGK_ERR_UNSUPPORTED before any GPU work.
+ *
+ *   cfg     as for bgk_create (validated the same way; tile_cells honoured);
+ *           the work goes to cfg->cuda_stream
+ *   f_in    device pointer, state at time level n (STATE LAYOUT), read only
+ *   f_out   device pointer, state at level n+1 (same size, must not overlap
+ *           f_in)
+ *   mom_out device pointer, ncell*4 doubles: moments (n, ux, uy, theta) of
+ *           the post-streaming state, as bgk_moments(which = 1)
+ * The result equals bgk_set_state(f_in) + bgk_step(1) on a solver made from
+ * cfg.  The call synchronises cfg->cuda_stream before returning and reports
+ * BGK_ERR_NUMERIC like bgk_sync.  The first call on a device looks up the
+ * scratch array's device address for that device (make that first call
+ * before any stream capture).  All calls share the one scratch array and it
+ * keeps the last call's contents (the error flag is cleared and the tables
+ * rebuilt on every call): calls whose work overlaps on the GPU, from several
+ * threads or streams, race and must be serialised by the caller. */
+BGK_API bgk_status bgk_step_noalloc(const bgk_config* cfg, const double* f_in, double* f_out,
+                                    double* mom_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ EXPORTS = (
     "bgk_create", "bgk_destroy", "bgk_get_info", "bgk_init_maxwellian_step", "bgk_init_uniform",
     "bgk_set_state", "bgk_get_state", "bgk_step", "bgk_moments", "bgk_wall_fluxes", "bgk_sync",
     "bgk_rankine_hugoniot", "bgk_last_error", "bgk_status_string", "bgk_abi_version",
+    "bgk_step_noalloc",
 )
 
 
@@ -93,6 +94,7 @@ def lib() -> ctypes.CDLL:
             "bgk_last_error": ([], ctypes.c_char_p),
             "bgk_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "bgk_abi_version": ([], ctypes.c_int),
+            "bgk_step_noalloc": ([ctypes.POINTER(bgk_config), _P, _P, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -209,3 +211,14 @@ def bgk_status_string(st: int) -> str:
 
 def bgk_abi_version() -> int:
     return lib().bgk_abi_version()
+
+
+def bgk_step_noalloc(cfg: bgk_config, f_in, f_out, mom_out) -> None:
+    """One step f_in -> f_out (device tensors) with no device allocation by the
+    library, for callers that must not have it call cudaMalloc; see bgk.h."""
+    a, da = _ptr(f_in)
+    b, db = _ptr(f_out)
+    m, dm = _ptr(mom_out)
+    if not (da and db and dm):
+        raise ValueError("bgk_step_noalloc takes device buffers only")
+    _check(lib().bgk_step_noalloc(ctypes.byref(cfg), a, b, m), "bgk_step_noalloc")

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -607,3 +608,116 @@ bgk_status bgk_sync(bgk_solver* s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// bgk_step_noalloc: one step for callers that cannot allocate device memory.
+// Its scratch (per-velocity tables, boundary tables, error flag) lives in this
+// file-scope device array instead of cudaMalloc'ed buffers; host code reaches
+// it through the address cudaGetSymbolAddress returns for the current device.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 384 * 1024;  // about 120 bytes per velocity
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Device address of the scratch array on the current device (looked up once
+// per device, on the first call made with that device current).
+bgk_status noalloc_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(BGK_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = (unsigned char*)g_noalloc_ptr[dev];
+  return BGK_OK;
+}
+
+}  // namespace
+
+extern "C" bgk_status bgk_step_noalloc(const bgk_config* cfg, const double* f_in, double* f_out,
+                                       double* mom_out) {
+  BGK_GUARD_BEGIN
+  if (!cfg || !f_in || !f_out || !mom_out) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  bgk::Params P;
+  double maxc = 0.0;
+  bgk_status st = validate(cfg, &P, &maxc);
+  if (st != BGK_OK) return st;
+  const size_t elems = (size_t)P.nx * P.ny * P.nv;
+  const char *a = (const char*)f_in, *b = (const char*)f_out;
+  if (a < b + elems * sizeof(double2) && b < a + elems * sizeof(double2))
+    return fail(BGK_ERR_INVALID_ARG, "f_in and f_out overlap");
+
+  // scratch layout: tables then the error flag, each 256-byte aligned
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  const size_t o_cx = take(sizeof(double) * P.nvx), o_cy = take(sizeof(double) * P.nvy);
+  const size_t o_coef = take(sizeof(double4_32a) * P.nv), o_shift = take(sizeof(int) * P.nv);
+  const size_t o_cxy = take(sizeof(double2) * P.nv), o_vinfo = take(sizeof(int) * P.nv);
+  const size_t o_ghost = take(sizeof(double2) * bgk::kFaces * P.nv);
+  const size_t o_emit = take(sizeof(double) * bgk::kFaces), o_err = take(sizeof(int));
+  if (off > kNoAllocScratchBytes)
+    return fail(BGK_ERR_UNSUPPORTED, "bgk_step_noalloc: tables need %zu bytes, the scratch holds %zu",
+                off, kNoAllocScratchBytes);
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(BGK_ERR_UNSUPPORTED, "libbgk is built for sm_103a only (device %s is sm_%d%d)",
+                prop.name, prop.major, prop.minor);
+  if (P.tile == 0) P.tile = auto_tile(P, prop.multiProcessorCount);
+  unsigned char* base = nullptr;
+  st = noalloc_scratch(dev, &base);
+  if (st != BGK_OK) return st;
+
+  bgk::Tables T;
+  double* cx = (double*)(base + o_cx);
+  double* cy = (double*)(base + o_cy);
+  double4_32a* coef = (double4_32a*)(base + o_coef);
+  int* shift = (int*)(base + o_shift);
+  double2* cxy = (double2*)(base + o_cxy);
+  int* vinfo = (int*)(base + o_vinfo);
+  double2* ghost = (double2*)(base + o_ghost);
+  double* emitted = (double*)(base + o_emit);
+  int* err = (int*)(base + o_err);
+  T.cx = cx;
+  T.cy = cy;
+  T.coef = coef;
+  T.shift = shift;
+  T.cxy = cxy;
+  T.vinfo = vinfo;
+  T.ghost = ghost;
+  T.emitted = emitted;
+
+  cudaStream_t stream = (cudaStream_t)cfg->cuda_stream;
+  e = cudaMemsetAsync(err, 0, sizeof(int), stream);
+  if (e == cudaSuccess) e = bgk::launch_build_tables(P, cx, cy, coef, shift, cxy, vinfo, ghost, emitted, stream);
+  if (e == cudaSuccess) e = bgk::prepare_step_f64(P);
+  if (e == cudaSuccess)
+    e = bgk::launch_step_f64(P, T, (const double2*)f_in, (double2*)f_out, (double4_32a*)mom_out, err, stream);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bgk_step_noalloc");
+  if (h & bgk::ERR_MOMENT) return fail(BGK_ERR_NUMERIC, "a cell reached n <= 0, theta <= 0 or a non-finite moment");
+  if (h & bgk::ERR_EFFECTIVE) return fail(BGK_ERR_NUMERIC, "the effective-parameter iteration did not converge in a cell");
+  return BGK_OK;
+  BGK_GUARD_END
+}
