@@ -35,7 +35,13 @@ FP64_NOMINAL_FLOPS = 1.25e12   # GB300 FP64 peak from the unit counts and clocks
 # FMA = 2: stream 2 x (mul + 2 fma) = 10, moments 1 + 2 + 2 + 3 = 8,
 # relaxation 2 x (mul + fma) = 6 (2D); 1D: stream 6, moments 6, relaxation 6.
 FLOPS_PER_UPDATE = {1: 18.0, 2: 24.0}
-BYTES_PER_UPDATE = {"f64": 32.0}  # read f^n once, write f^{n+1} once (g and h)
+# read f^n once, write f^{n+1} once (g and h): 2 x 2 values of the storage type
+BYTES_PER_UPDATE = {"f64": 32.0, "f32": 16.0, "bf16": 8.0}
+PRECISION = {"f64": 0, "f32": 1, "bf16": 2}
+DTYPE = {"f64": "f64", "f32": "f32", "bf16": "bf16"}
+DETAIL = {"f64": "FP64 state and arithmetic",
+          "f32": "FP32 state and streaming/relaxation; float-float moment sums finished in FP64; FP64 per-cell parameters",
+          "bf16": "BF16 deviation from the absolute Maxwellian; FP32 arithmetic; float-float moment sums finished in FP64; FP64 per-cell parameters"}
 
 
 def load_peaks() -> dict:
@@ -136,7 +142,9 @@ def workload(name: str) -> dict:
     if name in ("shock", W.SHOCK_M2["name"]):
         return W.SHOCK_M2
     if name in ("cavity256_f64", "cavity256"):
-        return W.scaled(W.CAVITY_256, steps=200, name="cavity_kn0.05_ma0.05_256x256_v48x48_f64_200steps")
+        return W.scaled(W.CAVITY_256, steps=200, name="cavity_kn0.05_ma0.05_256x256_v48x48_200steps")
+    if name == "cavity256_full":
+        return W.CAVITY_256
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -209,11 +217,12 @@ def ours_arm(args, w, world, rank, local, pg):
     ncell, nv, dim = sizes(w)
     nsteps = w["steps"]
 
+    prec = PRECISION[args.precision]
     if w["kind"] == "shock":
-        s = solver.make_shock(w, stream=stream.cuda_stream, tile_cells=args.tile)
+        s = solver.make_shock(w, stream=stream.cuda_stream, tile_cells=args.tile, precision=prec)
     else:
         xi = W.perturbation(w.get("seed", 0), ncell, nv)
-        s = solver.make_cavity(w, xi=xi, stream=stream.cuda_stream, tile_cells=args.tile)
+        s = solver.make_cavity(w, xi=xi, stream=stream.cuda_stream, tile_cells=args.tile, precision=prec)
     f0_host = torch.empty((ncell, nv, 2), dtype=torch.float64, pin_memory=True)
     B.bgk_get_state(s.h, f0_host.numpy())
     f0_dev = f0_host.to(f"cuda:{local}")
@@ -275,8 +284,8 @@ def ours_arm(args, w, world, rank, local, pg):
                "d2h_bytes_per_step": int(mom_host.numel() * 8)}
 
     peaks = load_peaks()
-    bytes_launch = BYTES_PER_UPDATE["f64"] * ncell * nv
-    flops_launch = FLOPS_PER_UPDATE[dim] * ncell * nv
+    bytes_launch = BYTES_PER_UPDATE[args.precision] * ncell * nv
+    flops_launch = FLOPS_PER_UPDATE[dim] * ncell * nv if args.precision == "f64" else 0.0
     hbm_achieved = bytes_launch / per_launch / 1e9
     alu_achieved = flops_launch / per_launch / 1e12
     t_hbm = bytes_launch / (peaks["hbm_gbs"] * 1e9)
@@ -288,7 +297,8 @@ def ours_arm(args, w, world, rank, local, pg):
     else:
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peaks["source"]}
-    roof.update({"traffic": args.traffic, "kernel": "bgk::step_f64_kernel",
+    kname = "bgk::step_f64_kernel" if args.precision == "f64" else "bgk::step_mixed_kernel"
+    roof.update({"traffic": args.traffic, "kernel": kname,
                  "launch_ms": per_launch * 1e3, "hbm_gbs": hbm_achieved,
                  "hbm_frac": hbm_achieved / peaks["hbm_gbs"], "fp64_tflops": alu_achieved})
 
@@ -303,16 +313,58 @@ def ours_arm(args, w, world, rank, local, pg):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": w["name"], "cells": ncell, "velocities": nv, "time_steps": nsteps,
                        "tile_cells": int(s.info.tile_cells),
-                       "precision": "f64", "parallelism": f"replica x{world}",
+                       "precision": args.precision, "arithmetic": DETAIL[args.precision],
+                       "parallelism": f"replica x{world}",
                        "l2": "flushed (256 MB write) between timed steps"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
     s.close()
+
+
+def accuracy_arm(args, w):
+    """Per-field error of a reduced-precision run against the FP64 GPU path
+    (which matches the CPU oracle to 1e-12 on every configuration the oracle
+    can finish): n, U, theta of every cell and the lid's mean shear flux."""
+    import torch
+
+    from paper_0903_4044_gb300 import bgk as B
+    from paper_0903_4044_gb300 import build, solver
+    from paper_0903_4044_gb300 import workloads as W
+
+    build.build()
+    torch.cuda.set_device(0)
+    ncell, nv, _ = sizes(w)
+    xi = W.perturbation(w.get("seed", 0), ncell, nv)
+    out = {}
+    for name in ("f64", args.precision):
+        s = solver.make_cavity(w, xi=xi, precision=PRECISION[name])
+        t0 = time.perf_counter()
+        s.step(w["steps"])
+        mom = s.moments()
+        lid = s.wall_fluxes(B.BGK_FACE_YHI)
+        out[name] = (mom, lid, time.perf_counter() - t0)
+        s.close()
+    (m64, l64, t64), (mr, lr, tr) = out["f64"], out[args.precision]
+    uw = w["lid_mach"] * (5.0 / 6.0) ** 0.5
+    shear64, shear = float(l64[:, 1].mean()), float(lr[:, 1].mean())
+    line = {
+        "mode": "accuracy", "workload": w["name"], "precision": args.precision, "time_steps": w["steps"],
+        "reference": "FP64 GPU path (oracle parity 1e-12)",
+        "err_n_rel_max": float(np.abs(mr[:, 0] - m64[:, 0]).max() / np.abs(m64[:, 0]).max()),
+        "err_u_over_lid_speed_max": float(np.abs(mr[:, 1:3] - m64[:, 1:3]).max() / uw),
+        "err_theta_rel_max": float(np.abs(mr[:, 3] - m64[:, 3]).max() / np.abs(m64[:, 3]).max()),
+        "err_u_over_lid_speed_rms": float(np.sqrt(((mr[:, 1:3] - m64[:, 1:3]) ** 2).mean()) / uw),
+        "lid_shear_f64": shear64, "lid_shear": shear,
+        "err_lid_shear_rel": abs(shear - shear64) / abs(shear64),
+        "mass_drift_rel": float(abs(mr[:, 0].sum() - m64[:, 0].sum()) / m64[:, 0].sum()),
+        "seconds": {"f64": t64, args.precision: tr},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -329,12 +381,19 @@ def main():
                     help="override the workload's time steps per benchmark step (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--tile", type=int, default=0, help="cells per CTA of the step kernel (0 = library choice)")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="report per-field errors of --precision against the FP64 path instead of timing")
+    ap.add_argument("--precision", default="f64", choices=sorted(PRECISION),
+                    help="state storage: f64, f32, or bf16 deviation from the absolute Maxwellian")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
     w = workload(args.workload)
     if args.time_steps is not None:
         w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
-    if args.impl == "reference":
+    if args.accuracy:
+        if rank == 0:
+            accuracy_arm(args, w)
+    elif args.impl == "reference":
         reference_arm(args, w, rank, pg)
     else:
         ours_arm(args, w, world, rank, local, pg)

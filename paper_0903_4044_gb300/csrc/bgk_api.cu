@@ -47,8 +47,10 @@ struct bgk_solver {
   int device = 0;
   cudaStream_t stream = nullptr;      // caller's stream (may be the legacy default)
   cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
-  double2* f[2] = {nullptr, nullptr};
+  int prec = bgk::PREC_F64;
+  void* f[2] = {nullptr, nullptr};  // state ping-pong, storage type by precision
   int cur = 0;
+  double2* stage = nullptr;  // FP64 view of the state (reduced precisions only)
   double4_32a* mom_step = nullptr;  // moments of the last post-streaming state
   double4_32a* mom_tmp = nullptr;   // scratch for bgk_moments(which = 0)
   double4_32a* flux_tmp = nullptr;  // scratch for bgk_wall_fluxes
@@ -60,6 +62,13 @@ struct bgk_solver {
   int* vinfo = nullptr;
   double2* ghost = nullptr;
   double* emitted = nullptr;
+  // FP32 tables of the reduced-precision step
+  float4* m_coef = nullptr;
+  float* m_cx = nullptr;
+  float* m_cy = nullptr;
+  float2* m_ghost = nullptr;
+  float2* m_mabs = nullptr;
+  double* m_sums = nullptr;  // [12]: mabs sums, emitted, mabs sums as float-float pairs
   int* err = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int64_t steps_done = 0;
@@ -78,7 +87,31 @@ struct bgk_solver {
     T.emitted = emitted;
     return T;
   }
+  bgk::MixedTables mtables() const {
+    bgk::MixedTables M;
+    M.coef = m_coef;
+    M.vinfo = vinfo;
+    M.cx = m_cx;
+    M.cy = m_cy;
+    M.ghost = m_ghost;
+    M.mabs = m_mabs;
+    M.mabs_sums = m_sums;
+    M.emitted = m_sums + 4;
+    M.mabs_ff = reinterpret_cast<const float2*>(m_sums + 8);
+    return M;
+  }
   size_t state_elems() const { return (size_t)P.nx * P.ny * P.nv; }  // (g,h) pairs
+  size_t point_bytes() const { return prec == bgk::PREC_F64 ? 16 : prec == bgk::PREC_F32 ? 8 : 4; }
+  // FP64 (g, h) view of the current state: the state itself in FP64, else
+  // converted into the staging buffer
+  cudaError_t f64_view(const double2** out) {
+    if (prec == bgk::PREC_F64) {
+      *out = (const double2*)f[cur];
+      return cudaSuccess;
+    }
+    *out = stage;
+    return bgk::launch_to_f64(P, prec, mtables(), f[cur], stage, stream);
+  }
 };
 
 namespace {
@@ -94,6 +127,10 @@ double max_abs_centre(double vmin, double vmax, int n) {
   double m = 0.0;
   for (int j = 0; j < n; ++j) m = std::fmax(m, std::fabs(vmin + (j + 0.5) * dc));
   return m;
+}
+
+size_t step_smem(const bgk::Params& P, int prec, int tile) {
+  return prec == BGK_F64 ? bgk::step_f64_smem_bytes(P, tile) : bgk::step_mixed_smem_bytes(P, tile);
 }
 
 // All configuration checks, before any CUDA call.  Fills P and max_courant.
@@ -129,10 +166,23 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
   if (c->tile_cells != 0 && c->tile_cells != 1 && c->tile_cells != 2 && c->tile_cells != 4 &&
       c->tile_cells != 8)
     return fail(BGK_ERR_INVALID_ARG, "tile_cells must be 0, 1, 2, 4 or 8 (got %d)", c->tile_cells);
-  if (c->precision != BGK_F64) {
-    if (c->precision == BGK_F32 || c->precision == BGK_BF16_DEV)
-      return fail(BGK_ERR_UNSUPPORTED, "precision %d is not built yet", c->precision);
+  if (c->precision != BGK_F64 && c->precision != BGK_F32 && c->precision != BGK_BF16_DEV)
     return fail(BGK_ERR_INVALID_ARG, "unknown precision %d", c->precision);
+  if (c->precision != BGK_F64) {
+    // the reduced-precision kernel streams 4 consecutive velocities of one
+    // row per lane: rows of a multiple of 8 with c_x changing sign only on
+    // multiples of 4
+    if (c->dim != 2)
+      return fail(BGK_ERR_UNSUPPORTED, "reduced precision is built for dim 2 only");
+    if (c->nvx % 8 != 0)
+      return fail(BGK_ERR_UNSUPPORTED, "reduced precision needs nvx a multiple of 8 (got %d)", c->nvx);
+    const double dc = (c->vx_max - c->vx_min) / c->nvx;
+    for (int j = 0; j < c->nvx; ++j) {
+      const double a = c->vx_min + (j + 0.5) * dc, b0 = c->vx_min + ((j & ~3) + 0.5) * dc;
+      if ((a > 0.0) != (b0 > 0.0) || (a < 0.0) != (b0 < 0.0))
+        return fail(BGK_ERR_UNSUPPORTED,
+                    "reduced precision needs c_x to change sign on a multiple of 4 velocities");
+    }
   }
 
   bgk::Params& p = *P;
@@ -168,12 +218,15 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
   // cells per CTA: the caller's choice (checked here), else chosen in
   // bgk_create once the device's SM count is known
   p.tile = c->tile_cells;
-  if (c->tile_cells && bgk::step_f64_smem_bytes(p, p.tile) > kMaxSmem)
+  if (c->tile_cells && c->precision != BGK_F64 && bgk::mixed_groups_per_lane(p, p.tile) == 0)
+    return fail(BGK_ERR_UNSUPPORTED, "tile_cells = %d leaves more than 24 velocities per lane", p.tile);
+  if (c->tile_cells && c->precision != BGK_F64) p.mgl = bgk::mixed_groups_per_lane(p, p.tile);
+  if (c->tile_cells && step_smem(p, c->precision, p.tile) > kMaxSmem)
     return fail(BGK_ERR_UNSUPPORTED, "tile_cells = %d needs %zu bytes of shared memory (max %zu)",
-                p.tile, bgk::step_f64_smem_bytes(p, p.tile), kMaxSmem);
-  if (!c->tile_cells && bgk::step_f64_smem_bytes(p, 1) > kMaxSmem)
+                p.tile, step_smem(p, c->precision, p.tile), kMaxSmem);
+  if (!c->tile_cells && step_smem(p, c->precision, 1) > kMaxSmem)
     return fail(BGK_ERR_UNSUPPORTED, "one cell's state needs %zu bytes of shared memory (max %zu)",
-                bgk::step_f64_smem_bytes(p, 1), kMaxSmem);
+                step_smem(p, c->precision, 1), kMaxSmem);
 
   const int nfaces = c->dim == 2 ? 4 : 2;
   bool walls = false;
@@ -223,10 +276,14 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
 
 // Largest tile (cells per CTA) that keeps two CTAs' staged state within an
 // SM's shared memory and still gives every SM at least two CTAs.
-int auto_tile(const bgk::Params& P, int sms) {
+int auto_tile(const bgk::Params& P, int prec, int sms) {
   const long long ncell = (long long)P.nx * P.ny;
-  for (int t : {8, 4, 2})
-    if (bgk::step_f64_smem_bytes(P, t) <= kAutoSmem && (ncell + t - 1) / t >= 2LL * sms) return t;
+  for (int t : {8, 4, 2}) {
+    // reduced precisions: at most 16 velocities per lane (more spills registers)
+    if (prec != BGK_F64 && (bgk::mixed_groups_per_lane(P, t) == 0 || bgk::mixed_groups_per_lane(P, t) > 4))
+      continue;
+    if (step_smem(P, prec, t) <= kAutoSmem && (ncell + t - 1) / t >= 2LL * sms) return t;
+  }
   return 1;
 }
 
@@ -242,8 +299,9 @@ void release(bgk_solver* s) {
   if (!s) return;
   for (auto& g : s->graph)
     if (g) cudaGraphExecDestroy(g);
-  void* bufs[] = {s->f[0], s->f[1], s->mom_step, s->mom_tmp, s->flux_tmp, s->cx, s->cy, s->coef,
-                  s->shift, s->cxy, s->vinfo, s->ghost, s->emitted, s->err};
+  void* bufs[] = {s->f[0], s->f[1], s->stage, s->mom_step, s->mom_tmp, s->flux_tmp, s->cx, s->cy,
+                  s->coef, s->shift, s->cxy, s->vinfo, s->ghost, s->emitted, s->m_coef, s->m_cx,
+                  s->m_cy, s->m_ghost, s->m_mabs, s->m_sums, s->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -251,7 +309,19 @@ void release(bgk_solver* s) {
 }
 
 cudaError_t enqueue_step(bgk_solver* s, int from, cudaStream_t st) {
-  return bgk::launch_step_f64(s->P, s->tables(), s->f[from], s->f[1 - from], s->mom_step, s->err, st);
+  if (s->prec == bgk::PREC_F64)
+    return bgk::launch_step_f64(s->P, s->tables(), (const double2*)s->f[from], (double2*)s->f[1 - from],
+                                s->mom_step, s->err, st);
+  return bgk::launch_step_mixed(s->P, s->prec, s->mtables(), s->f[from], s->f[1 - from], s->mom_step,
+                                s->err, st);
+}
+
+// Write an FP64 state (device pointer, ABI layout) into the current buffer.
+cudaError_t store_f64(bgk_solver* s, const double2* src) {
+  if (s->prec == bgk::PREC_F64)
+    return cudaMemcpyAsync(s->f[s->cur], src, sizeof(double2) * s->state_elems(), cudaMemcpyDeviceToDevice,
+                           s->stream);
+  return bgk::launch_from_f64(s->P, s->prec, s->mtables(), src, s->f[s->cur], s->stream);
 }
 
 bgk_status ensure_graph(bgk_solver* s, int start) {
@@ -368,9 +438,11 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
     return fail(BGK_ERR_UNSUPPORTED, "libbgk is built for sm_103a only (device %s is sm_%d%d)",
                 prop.name, prop.major, prop.minor);
 
-  if (P.tile == 0) P.tile = auto_tile(P, prop.multiProcessorCount);
+  if (P.tile == 0) P.tile = auto_tile(P, cfg->precision, prop.multiProcessorCount);
+  if (cfg->precision != BGK_F64) P.mgl = bgk::mixed_groups_per_lane(P, P.tile);
 
   bgk_solver* s = new bgk_solver();
+  s->prec = cfg->precision;
   s->cfg = *cfg;
   s->P = P;
   s->device = dev;
@@ -388,8 +460,30 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
       return rs;                                       \
     }                                                  \
   } while (0)
-  ALLOC(f[0], elems);
-  ALLOC(f[1], elems);
+  {
+    const size_t bytes = s->point_bytes() * elems;
+    unsigned char *f0 = nullptr, *f1 = nullptr;
+    cudaError_t ae = dev_alloc(s, &f0, bytes);
+    if (ae == cudaSuccess) {
+      s->f[0] = f0;
+      ae = dev_alloc(s, &f1, bytes);
+      if (ae == cudaSuccess) s->f[1] = f1;
+    }
+    if (ae != cudaSuccess) {
+      bgk_status rs = cuda_fail(ae, "allocate state");
+      release(s);
+      return rs;
+    }
+  }
+  if (s->prec != bgk::PREC_F64) {
+    ALLOC(stage, elems);
+    ALLOC(m_coef, P.nv);
+    ALLOC(m_cx, P.nvx);
+    ALLOC(m_cy, P.nvy);
+    ALLOC(m_ghost, (size_t)bgk::kFaces * P.nv);
+    ALLOC(m_mabs, P.nv);
+    ALLOC(m_sums, 12);
+  }
   ALLOC(mom_step, ncell);
   ALLOC(mom_tmp, ncell);
   ALLOC(flux_tmp, nfc);
@@ -404,14 +498,15 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
   ALLOC(err, 1);
 #undef ALLOC
   e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->f[0], 0, sizeof(double2) * elems, s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->f[1], 0, sizeof(double2) * elems, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->f[0], 0, s->point_bytes() * elems, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->f[1], 0, s->point_bytes() * elems, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->mom_step, 0, sizeof(double4_32a) * ncell, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
   if (e == cudaSuccess)
     e = bgk::launch_build_tables(P, s->cx, s->cy, s->coef, s->shift, s->cxy, s->vinfo, s->ghost,
                                  s->emitted, s->stream);
-  if (e == cudaSuccess) e = bgk::prepare_step_f64(P);
+  if (e == cudaSuccess && s->prec != bgk::PREC_F64) e = bgk::launch_build_mixed_tables(P, s->tables(), s->mtables(), s->stream);
+  if (e == cudaSuccess) e = s->prec == bgk::PREC_F64 ? bgk::prepare_step_f64(P) : bgk::prepare_step_mixed(P, s->prec);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
     bgk_status rs = cuda_fail(e, "solver set-up");
@@ -466,7 +561,9 @@ bgk_status bgk_init_maxwellian_step(bgk_solver* s, double x_split, const double 
   bgk_status st = select_device(s);
   if (st != BGK_OK) return st;
   cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
-  if (e == cudaSuccess) e = bgk::launch_init_step(s->P, s->f[s->cur], x_split, left, right, s->stream);
+  double2* out = s->prec == bgk::PREC_F64 ? (double2*)s->f[s->cur] : s->stage;
+  if (e == cudaSuccess) e = bgk::launch_init_step(s->P, out, x_split, left, right, s->stream);
+  if (e == cudaSuccess && s->prec != bgk::PREC_F64) e = store_f64(s, s->stage);
   if (e != cudaSuccess) return cuda_fail(e, "init step profile");
   s->steps_done = 0;
   return BGK_OK;
@@ -483,19 +580,23 @@ bgk_status bgk_init_uniform(bgk_solver* s, const double state[4], const double* 
   bgk_status st = select_device(s);
   if (st != BGK_OK) return st;
   const size_t bytes = sizeof(double2) * s->state_elems();
+  const bool f64 = s->prec == bgk::PREC_F64;
+  double2* out = f64 ? (double2*)s->f[s->cur] : s->stage;
   const double2* dxi = nullptr;
   cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
   if (e == cudaSuccess && xi) {
     if (xi_on_device) {
       dxi = (const double2*)xi;
     } else {
-      // stage the host perturbation in the idle state buffer
-      double2* stage = s->f[1 - s->cur];
-      e = cudaMemcpyAsync(stage, xi, bytes, cudaMemcpyHostToDevice, s->stream);
-      dxi = stage;
+      // stage the host perturbation on the device: in the idle FP64 state
+      // buffer, or in the FP64 view that the kernel then overwrites in place
+      double2* buf = f64 ? (double2*)s->f[1 - s->cur] : s->stage;
+      e = cudaMemcpyAsync(buf, xi, bytes, cudaMemcpyHostToDevice, s->stream);
+      dxi = buf;
     }
   }
-  if (e == cudaSuccess) e = bgk::launch_init_uniform(s->P, s->f[s->cur], state, dxi, amplitude, s->stream);
+  if (e == cudaSuccess) e = bgk::launch_init_uniform(s->P, out, state, dxi, amplitude, s->stream);
+  if (e == cudaSuccess && !f64) e = store_f64(s, s->stage);
   if (e == cudaSuccess && xi && !xi_on_device) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "init uniform state");
   s->steps_done = 0;
@@ -510,9 +611,17 @@ bgk_status bgk_set_state(bgk_solver* s, const double* f, int on_device) {
   if (st != BGK_OK) return st;
   const size_t bytes = sizeof(double2) * s->state_elems();
   cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->f[s->cur], f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                        s->stream);
+  if (e == cudaSuccess) {
+    if (s->prec == bgk::PREC_F64) {
+      e = cudaMemcpyAsync(s->f[s->cur], f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          s->stream);
+    } else if (on_device) {
+      e = store_f64(s, (const double2*)f);
+    } else {
+      e = cudaMemcpyAsync(s->stage, f, bytes, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = store_f64(s, s->stage);
+    }
+  }
   // a host source may be reused as soon as the call returns
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set_state copy");
@@ -527,8 +636,16 @@ bgk_status bgk_get_state(bgk_solver* s, double* f, int on_device) {
   bgk_status st = select_device(s);
   if (st != BGK_OK) return st;
   const size_t bytes = sizeof(double2) * s->state_elems();
-  cudaError_t e = cudaMemcpyAsync(f, s->f[s->cur], bytes,
-                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+  cudaError_t e;
+  if (s->prec != bgk::PREC_F64 && on_device) {
+    e = bgk::launch_to_f64(s->P, s->prec, s->mtables(), s->f[s->cur], (double2*)f, s->stream);
+  } else {
+    const double2* view = nullptr;
+    e = s->f64_view(&view);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(f, view, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          s->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "get_state copy");
   return check_flag(s);
   BGK_GUARD_END
@@ -569,8 +686,16 @@ bgk_status bgk_moments(bgk_solver* s, int which, double* mom, int on_device) {
   const size_t ncell = (size_t)s->P.nx * s->P.ny;
   cudaError_t e = cudaSuccess;
   const double4_32a* src = s->mom_step;
+  if (which == 1 && s->prec != bgk::PREC_F64) {
+    // the reduced-precision step publishes float-float velocity sums
+    e = bgk::launch_msum_moments(s->P, s->prec, s->mtables(), (const float2*)s->mom_step, s->mom_tmp,
+                                 s->stream);
+    src = s->mom_tmp;
+  }
   if (which == 0) {
-    e = bgk::launch_moments(s->P, s->tables(), s->f[s->cur], s->mom_tmp, s->stream);
+    const double2* view = nullptr;
+    e = s->f64_view(&view);
+    if (e == cudaSuccess) e = bgk::launch_moments(s->P, s->tables(), view, s->mom_tmp, s->stream);
     src = s->mom_tmp;
   }
   if (e == cudaSuccess)
@@ -589,7 +714,9 @@ bgk_status bgk_wall_fluxes(bgk_solver* s, int face, double* out, int on_device) 
   bgk_status st = select_device(s);
   if (st != BGK_OK) return st;
   const int ncells = (face < 2) ? s->P.ny : s->P.nx;
-  cudaError_t e = bgk::launch_wall_fluxes(s->P, s->tables(), s->f[s->cur], face, s->flux_tmp, s->stream);
+  const double2* view = nullptr;
+  cudaError_t e = s->f64_view(&view);
+  if (e == cudaSuccess) e = bgk::launch_wall_fluxes(s->P, s->tables(), view, face, s->flux_tmp, s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, s->flux_tmp, sizeof(double4_32a) * ncells,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
@@ -652,6 +779,8 @@ extern "C" bgk_status bgk_step_noalloc(const bgk_config* cfg, const double* f_in
   double maxc = 0.0;
   bgk_status st = validate(cfg, &P, &maxc);
   if (st != BGK_OK) return st;
+  if (cfg->precision != BGK_F64)
+    return fail(BGK_ERR_UNSUPPORTED, "bgk_step_noalloc takes BGK_F64 states only");
   const size_t elems = (size_t)P.nx * P.ny * P.nv;
   const char *a = (const char*)f_in, *b = (const char*)f_out;
   if (a < b + elems * sizeof(double2) && b < a + elems * sizeof(double2))
@@ -682,7 +811,7 @@ extern "C" bgk_status bgk_step_noalloc(const bgk_config* cfg, const double* f_in
   if (prop.major != 10 || prop.minor != 3)
     return fail(BGK_ERR_UNSUPPORTED, "libbgk is built for sm_103a only (device %s is sm_%d%d)",
                 prop.name, prop.major, prop.minor);
-  if (P.tile == 0) P.tile = auto_tile(P, prop.multiProcessorCount);
+  if (P.tile == 0) P.tile = auto_tile(P, BGK_F64, prop.multiProcessorCount);
   unsigned char* base = nullptr;
   st = noalloc_scratch(dev, &base);
   if (st != BGK_OK) return st;

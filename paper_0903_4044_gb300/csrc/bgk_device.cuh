@@ -114,6 +114,114 @@ __device__ __forceinline__ bool moments_ok(const double q[4]) {
          isfinite(q[3]);
 }
 
+// ---------------------------------------------------------------------------
+// Effective Maxwellian parameters (Sec. 2.1, remark after Eq. exact): find p
+// with D(p) = q, D = discrete moments of the reduced Maxwellian, by
+// p <- p + (q - D(p)) from p = q.  D is evaluated from central sums
+// M_m = sum_j d^m e_j, d = c_j - u_b, e_j = exp(-d^2/theta_b) of each axis,
+// taken at a base point b, and moved to p to first order:
+//   e_j(p) = e_j(b) (1 + d (w1 + d w2)), w1 = 2 (u - u_b)/theta_b,
+//   w2 = (theta - theta_b)/theta_b^2,
+// so that with S_m = M_m + w1 M_{m+1} + w2 M_{m+2} per axis
+//   n_d = n (pi theta)^(-d/2) dv Sx0 Sy0,  U_d = u_b + S1/S0,
+//   theta_d = (2/3) (sum over axes of (S2/S0 - (S1/S0)^2) + kappa),
+// kappa = theta (dim 1) or theta/2 (dim 2) being the h part per unit
+// density.  When p has moved more than kLinMax from b the caller
+// re-evaluates the Gaussians at b = p (reeval).  Every lane runs its own
+// cell; the loop has no cross-lane operations.
+// ---------------------------------------------------------------------------
+struct EffState {
+  double base[4], p[4];
+  int it;
+  bool conv, fail, reeval;
+};
+
+__device__ __forceinline__ void eff_init(EffState& E, const double q[4], bool done) {
+  for (int k = 0; k < 4; ++k) E.base[k] = E.p[k] = q[k];
+  E.it = 0;
+  E.conv = done;
+  E.fail = false;
+  E.reeval = false;
+}
+
+template <int DIM>
+__device__ __forceinline__ void eff_iterate(const Params& P, const double q[4], const double Mx[5],
+                                            const double My[5], EffState& E, double lin_max = kLinMax,
+                                            double tol = kEffTol) {
+  const double vs = sqrt(q[3]);
+  double* p = E.p;
+  double* b = E.base;
+  while (!E.conv && !E.fail && !E.reeval) {
+    ++E.it;
+    const double ith = 1.0 / b[3];
+    const double w2 = (p[3] - b[3]) * ith * ith;
+    double Sx[3], Sy[3] = {1.0, 0.0, 0.0};
+    const double w1x = 2.0 * (p[1] - b[1]) * ith;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) Sx[m] = Mx[m] + w1x * Mx[m + 1] + w2 * Mx[m + 2];
+    if (DIM == 2) {
+      const double w1y = 2.0 * (p[2] - b[2]) * ith;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) Sy[m] = My[m] + w1y * My[m + 1] + w2 * My[m + 2];
+    }
+    const double pref = (DIM == 1) ? p[0] / sqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
+    const double rx = 1.0 / Sx[0], ry = 1.0 / Sy[0];
+    const double mux = Sx[1] * rx, muy = Sy[1] * ry;
+    double d[4];
+    d[0] = pref * P.dv * Sx[0] * Sy[0];
+    d[1] = b[1] + mux;
+    d[2] = (DIM == 2) ? b[2] + muy : 0.0;
+    const double kappa = (DIM == 1) ? p[3] : 0.5 * p[3];
+    const double var = (Sx[2] * rx - mux * mux) + ((DIM == 2) ? (Sy[2] * ry - muy * muy) : 0.0);
+    d[3] = (2.0 / 3.0) * (var + kappa);
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double delta = q[k] - d[k];
+      p[k] += delta;
+      const double scale = (k == 0) ? q[0] : (k == 3) ? q[3] : vs;
+      r = fmax(r, fabs(delta) / scale);
+    }
+    if (!(p[0] > 0.0) || !(p[3] > 0.0) || !isfinite(r)) {
+      E.fail = true;
+    } else if (r < tol) {
+      E.conv = true;
+    } else if (E.it >= kEffMaxIt) {
+      if (r < kEffFail) E.conv = true;
+      else E.fail = true;
+    }
+    if (!E.fail) {
+      const double drift = fmax(fmax(fabs(p[0] - b[0]) / b[0], fabs(p[3] - b[3]) / b[3]),
+                                fmax(fabs(p[1] - b[1]), fabs(p[2] - b[2])) / sqrt(b[3]));
+      if (drift > lin_max) {
+        for (int k = 0; k < 4; ++k) b[k] = p[k];
+        E.reeval = true;
+      }
+    }
+  }
+}
+
+// First-order factors that move the Gaussians from E.base to E.p.
+__device__ __forceinline__ void eff_lin(const EffState& E, double& w1x, double& w1y, double& w2) {
+  const double ith = 1.0 / E.base[3];
+  w2 = (E.p[3] - E.base[3]) * ith * ith;
+  w1x = 2.0 * (E.p[1] - E.base[1]) * ith;
+  w1y = 2.0 * (E.p[2] - E.base[2]) * ith;
+}
+
+// Relaxation weights from nu = n theta^(1-omega): exact (Eq. relaxation)
+// b = exp(-nu dt), a = 1 - b; Euler a = nu dt, b = 1 - a.
+__device__ __forceinline__ void relax_weights(const Params& P, const double q[4], double& a, double& b) {
+  const double nu = q[0] * (P.omega == 0.5 ? sqrt(q[3]) : pow(q[3], 1.0 - P.omega));
+  if (P.relax_exact) {
+    b = exp(-nu * P.dt);
+    a = 1.0 - b;
+  } else {
+    a = P.dt * nu;
+    b = 1.0 - a;
+  }
+}
+
 // Boundary value (g, h) just outside `face` at velocity j: the inflow
 // Maxwellian, n_W times the unit wall Maxwellian, or the mirror image of the
 // wall-adjacent cell's own state `fc` (specular).

@@ -11,6 +11,7 @@ constexpr int kMaxNv = 4096;   // velocities per cell handled by one CTA
 constexpr int kFaces = 4;
 enum { XLO = 0, XHI = 1, YLO = 2, YHI = 3 };
 enum { BC_INFLOW = 0, BC_DIFFUSE = 1, BC_SPECULAR = 2 };
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_BF16 = 2 };  // as bgk_precision
 
 // Error bits written by kernels into the solver's device flag.
 enum { ERR_MOMENT = 1, ERR_EFFECTIVE = 2 };
@@ -30,6 +31,7 @@ constexpr double kLinMax = 1e-8;
 struct Params {
   int dim, nx, ny, nvx, nvy, nv;
   int tile;  // spatial cells per CTA of the step kernel (1, 2, 4 or 8)
+  int mgl;   // reduced precisions: groups of 4 velocities per lane (2, 4 or 6)
   int conservative, relax_exact;
   int bc_kind[kFaces];
   double dt, dx, dy, dcx, dcy, dv;
@@ -52,7 +54,20 @@ struct Tables {
   const double* emitted;  // [kFaces] sum_{c_n>0} c_n G_W(n=1) dv (diffuse)
 };
 
-// Launchers (bgk_step.cu, bgk_aux.cu).  All enqueue on `stream`.
+// FP32 tables of the reduced-precision step (bgk_mixed.cu).
+struct MixedTables {
+  const float4* coef;       // [nv] (ax, ay, c_x, c_y): flux-form streaming weights
+  const int* vinfo;         // [nv] as Tables::vinfo
+  const float* cx;          // [nvx]
+  const float* cy;          // [nvy]
+  const float2* ghost;      // [kFaces][nv] FP32 boundary Maxwellians
+  const float2* mabs;       // [nv] absolute Maxwellian (n = 1, U = 0, theta = 1) in FP32
+  const double* mabs_sums;  // [4] FP64 sums of mabs: g, c_x g, c_y g, |c|^2 g + h
+  const float2* mabs_ff;    // [4] the same sums as float-float pairs
+  const double* emitted;    // [kFaces] sum_{c_n>0} c_n ghost_g dv of the FP32 ghosts
+};
+
+// Launchers (bgk_step.cu, bgk_aux.cu, bgk_mixed.cu).  All enqueue on `stream`.
 cudaError_t launch_step_f64(const Params& P, const Tables& T, const double2* fin, double2* fout,
                             double4_32a* mom, int* err, cudaStream_t stream);
 cudaError_t launch_build_tables(const Params& P, double* cx, double* cy, double4_32a* coef, int* shift,
@@ -68,5 +83,18 @@ cudaError_t launch_moments(const Params& P, const Tables& T, const double2* f, d
                            cudaStream_t stream);
 cudaError_t launch_wall_fluxes(const Params& P, const Tables& T, const double2* f, int face,
                                double4_32a* out, cudaStream_t stream);
+cudaError_t launch_build_mixed_tables(const Params& P, const Tables& T, const MixedTables& M,
+                                      cudaStream_t stream);
+size_t step_mixed_smem_bytes(const Params& P, int tile);
+int mixed_groups_per_lane(const Params& P, int tile);
+cudaError_t launch_msum_moments(const Params& P, int prec, const MixedTables& M, const float2* msum,
+                                double4_32a* mom, cudaStream_t stream);
+cudaError_t prepare_step_mixed(const Params& P, int prec);
+cudaError_t launch_step_mixed(const Params& P, int prec, const MixedTables& M, const void* fin, void* fout,
+                              double4_32a* mom, int* err, cudaStream_t stream);
+cudaError_t launch_to_f64(const Params& P, int prec, const MixedTables& M, const void* f, double2* out,
+                          cudaStream_t stream);
+cudaError_t launch_from_f64(const Params& P, int prec, const MixedTables& M, const double2* in, void* f,
+                            cudaStream_t stream);
 
 }  // namespace bgk

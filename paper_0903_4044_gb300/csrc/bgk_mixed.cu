@@ -1,0 +1,736 @@
+// bgk_mixed.cu - the reduced-precision BGK step (2D): the state is stored as
+// FP32 (g, h) pairs, or as BF16 deviations (dg, dh) from the absolute
+// Maxwellian M_abs (n = 1, U = 0, theta = 1), and streamed and relaxed on the
+// FP32 pipe; moment sums are carried in FP32 pairs by error-free
+// transformations (Kahan per lane, TwoSum across lanes) and finished in FP64;
+// the per-cell parameters (moments, nu, effective Maxwellian, normalisation)
+// are FP64 with cells in lanes; the Gaussian factors are FP32.
+//
+// Conservation in low precision: streaming uses the flux form
+// f~ = f - ax (f - f_upx) - ay (f - f_upy), which telescopes whatever the
+// rounded weights, and relaxation uses f^{n+1} = f~ + (a Phi - a f~), whose
+// mass change is only the rounding of each term (no systematic drift from
+// weights that do not sum to 1).
+//
+// G cells per CTA, one warp per cell, each lane handling 4 consecutive
+// velocities (one row, one sign of c_x and c_y: the velocity grid has
+// nvx % 8 == 0 and sign changes on multiples of 4, checked on the host).
+// Unlike the FP64 kernel, f~ is not staged in shared memory: the FP32
+// streaming is recomputed in the relaxation pass from inputs that are still
+// in L1/L2, which keeps shared memory free for many resident warps (the FP32
+// arithmetic is cheap; shared-memory capacity per cell was the limit).
+#include <cuda_bf16.h>
+
+#include "bgk_device.cuh"
+
+namespace bgk {
+
+namespace {
+
+__device__ __forceinline__ int vi_jx(int vi) { return vi & 0xfff; }
+__device__ __forceinline__ int vi_jy(int vi) { return (vi >> 12) & 0xfff; }
+__device__ __forceinline__ int vi_sx(int vi) { return ((vi >> 24) & 3) - 1; }
+__device__ __forceinline__ int vi_sy(int vi) { return ((vi >> 26) & 3) - 1; }
+
+// ---- error-free FP32 arithmetic ----------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+// (h, l) += (bh, bl), renormalised
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e += l + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+// Kahan: (s, c) accumulates x; the sum is s - c
+__device__ __forceinline__ void kahan(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+__device__ __forceinline__ void ff_xor(float& h, float& l, int m) {
+  const float oh = __shfl_xor_sync(0xffffffffu, h, m);
+  const float ol = __shfl_xor_sync(0xffffffffu, l, m);
+  ff_add(h, l, oh, ol);
+}
+// Four float-float values per lane -> lane L holds the warp total of value
+// (L >> 3) & 3 (recursive halving, as warp_reduce4).
+__device__ __forceinline__ void warp_reduce4_ff(float (&h)[4], float (&l)[4], float& oh, float& ol) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8;
+  float ah[2], al[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float sh = __shfl_xor_sync(0xffffffffu, b4 ? h[k] : h[k + 2], 16);
+    const float sl = __shfl_xor_sync(0xffffffffu, b4 ? l[k] : l[k + 2], 16);
+    ah[k] = b4 ? h[k + 2] : h[k];
+    al[k] = b4 ? l[k + 2] : l[k];
+    ff_add(ah[k], al[k], sh, sl);
+  }
+  const float sh = __shfl_xor_sync(0xffffffffu, b3 ? ah[0] : ah[1], 8);
+  const float sl = __shfl_xor_sync(0xffffffffu, b3 ? al[0] : al[1], 8);
+  oh = b3 ? ah[1] : ah[0];
+  ol = b3 ? al[1] : al[0];
+  ff_add(oh, ol, sh, sl);
+  ff_xor(oh, ol, 4);
+  ff_xor(oh, ol, 2);
+  ff_xor(oh, ol, 1);
+}
+
+// ---- storage --------------------------------------------------------------
+template <int PREC>
+struct Store;
+
+template <>
+struct Store<PREC_F32> {
+  static constexpr bool delta = false;
+  __device__ static void load4(const void* base, size_t idx, float2 (&v)[4]) {
+    const float4* p = reinterpret_cast<const float4*>(static_cast<const float2*>(base) + idx);
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+    v[3] = make_float2(b.z, b.w);
+  }
+  __device__ static void store4(void* base, size_t idx, const float2 (&v)[4]) {
+    float4* p = reinterpret_cast<float4*>(static_cast<float2*>(base) + idx);
+    p[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    p[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+  }
+  __device__ static float2 load1(const void* base, size_t idx) {
+    return __ldg(static_cast<const float2*>(base) + idx);
+  }
+};
+
+template <>
+struct Store<PREC_BF16> {
+  static constexpr bool delta = true;
+  __device__ static float2 unpack(unsigned w) {
+    __nv_bfloat162 b;
+    memcpy(&b, &w, 4);
+    return __bfloat1622float2(b);
+  }
+  __device__ static unsigned pack(float2 v) {
+    const __nv_bfloat162 b = __float22bfloat162_rn(v);
+    unsigned w;
+    memcpy(&w, &b, 4);
+    return w;
+  }
+  __device__ static void load4(const void* base, size_t idx, float2 (&v)[4]) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(static_cast<const unsigned*>(base) + idx));
+    v[0] = unpack(u.x);
+    v[1] = unpack(u.y);
+    v[2] = unpack(u.z);
+    v[3] = unpack(u.w);
+  }
+  __device__ static void store4(void* base, size_t idx, const float2 (&v)[4]) {
+    *reinterpret_cast<uint4*>(static_cast<unsigned*>(base) + idx) =
+        make_uint4(pack(v[0]), pack(v[1]), pack(v[2]), pack(v[3]));
+  }
+  __device__ static float2 load1(const void* base, size_t idx) {
+    return unpack(__ldg(static_cast<const unsigned*>(base) + idx));
+  }
+};
+
+// Boundary value at velocity j in the stored representation (full value, or
+// deviation from M_abs for the BF16 form).
+template <int PREC>
+__device__ __forceinline__ float2 ghost_m(const Params& P, const MixedTables& M, int face, int j,
+                                          float nw, const void* fin, size_t c0) {
+  const int kind = P.bc_kind[face];
+  if (kind == BC_SPECULAR) {
+    const int vi = M.vinfo[j];
+    const int jx = vi_jx(vi), jy = vi_jy(vi);
+    const int jr = (face == XLO || face == XHI) ? jy * P.nvx + (P.nvx - 1 - jx)
+                                                : (P.nvy - 1 - jy) * P.nvx + jx;
+    return Store<PREC>::load1(fin, c0 + jr);  // M_abs is mirror symmetric
+  }
+  float2 g = M.ghost[face * P.nv + j];
+  if (kind == BC_DIFFUSE) g = make_float2(nw * g.x, nw * g.y);
+  if (Store<PREC>::delta) {
+    const float2 m = M.mabs[j];
+    g = make_float2(g.x - m.x, g.y - m.y);
+  }
+  return g;
+}
+
+// ---- the step --------------------------------------------------------------
+// A CTA holds G cells and 8 warps, WPC = 8/G warps per cell.  The velocities
+// of a cell come in groups of 4 consecutive indices (one row, one sign of c_x
+// and c_y); group k goes to lane k mod (32 WPC) of the cell's warps, at most
+// MGL groups per lane, and f~ of those groups stays in that lane's registers
+// from streaming (phase 1) to relaxation (phase 3).  Phase 2 runs on the
+// cell's first warp, on the FP32 pipe except the normalisation.
+
+// Where a cell sits: which faces it touches, and n_W of its diffuse faces.
+struct CellCtx {
+  size_t c0, row;
+  bool bxlo, bxhi, bylo, byhi, interior;
+  float nw[4];
+};
+
+// A1 for the 4 velocities j0..j0+3 of one cell, flux form
+//   f~ = f - ax (f - f_upx) - ay (f - f_upy)
+// in the stored representation (deviations for BF16).
+template <int PREC>
+__device__ __forceinline__ void stream_group(const Params& P, const MixedTables& M, const void* fin,
+                                             const CellCtx& C, int j0, float2 (&ft)[4]) {
+  using S = Store<PREC>;
+  const int nv = P.nv;
+  const int vi = M.vinfo[j0];
+  const int sgx = vi_sx(vi), sgy = vi_sy(vi);
+  float2 f0[4], fx[4], fy[4];
+  S::load4(fin, C.c0 + j0, f0);
+  if (C.interior) {
+    S::load4(fin, C.c0 - (ptrdiff_t)sgx * nv + j0, fx);
+    S::load4(fin, C.c0 - (ptrdiff_t)sgy * (ptrdiff_t)C.row + j0, fy);
+  } else {
+    if (sgx > 0 && !C.bxlo) S::load4(fin, C.c0 - nv + j0, fx);
+    else if (sgx < 0 && !C.bxhi) S::load4(fin, C.c0 + nv + j0, fx);
+    else if (sgx == 0) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) fx[p] = f0[p];
+    } else {
+      const int face = sgx > 0 ? XLO : XHI;
+      const float nw = sgx > 0 ? C.nw[XLO] : C.nw[XHI];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) fx[p] = ghost_m<PREC>(P, M, face, j0 + p, nw, fin, C.c0);
+    }
+    if (sgy > 0 && !C.bylo) S::load4(fin, C.c0 - C.row + j0, fy);
+    else if (sgy < 0 && !C.byhi) S::load4(fin, C.c0 + C.row + j0, fy);
+    else if (sgy == 0) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) fy[p] = f0[p];
+    } else {
+      const int face = sgy > 0 ? YLO : YHI;
+      const float nw = sgy > 0 ? C.nw[YLO] : C.nw[YHI];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) fy[p] = ghost_m<PREC>(P, M, face, j0 + p, nw, fin, C.c0);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float4 co = M.coef[j0 + p];  // (ax, ay, cx, cy)
+    ft[p].x = fmaf(-co.y, f0[p].x - fy[p].x, fmaf(-co.x, f0[p].x - fx[p].x, f0[p].x));
+    ft[p].y = fmaf(-co.y, f0[p].y - fy[p].y, fmaf(-co.x, f0[p].y - fx[p].y, f0[p].y));
+  }
+}
+
+// Cell context, with A0: n_W of each diffuse face from the incident flux
+// sum |c_n| g over c_n < 0 of the cell's own (full) state (every warp of the
+// cell computes it for itself).
+template <int PREC>
+__device__ __forceinline__ CellCtx cell_ctx(const Params& P, const MixedTables& M, const void* fin, int cell) {
+  using S = Store<PREC>;
+  const int lane = threadIdx.x & 31;
+  const int nv = P.nv, nx = P.nx;
+  const int ix = cell % nx, iy = cell / nx;
+  CellCtx C;
+  C.c0 = (size_t)cell * nv;
+  C.row = (size_t)nx * nv;
+  C.bxlo = ix == 0;
+  C.bxhi = ix == nx - 1;
+  C.bylo = iy == 0;
+  C.byhi = iy == P.ny - 1;
+  C.interior = !(C.bxlo || C.bxhi || C.bylo || C.byhi);
+  for (int f = 0; f < 4; ++f) C.nw[f] = 0.f;
+  unsigned diff = 0;
+  if (C.bxlo && P.bc_kind[XLO] == BC_DIFFUSE) diff |= 1u;
+  if (C.bxhi && P.bc_kind[XHI] == BC_DIFFUSE) diff |= 2u;
+  if (C.bylo && P.bc_kind[YLO] == BC_DIFFUSE) diff |= 4u;
+  if (C.byhi && P.bc_kind[YHI] == BC_DIFFUSE) diff |= 8u;
+  if (diff) {
+    float hs[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int j0 = 4 * lane; j0 < nv; j0 += 128) {
+      float2 v[4];
+      S::load4(fin, C.c0 + j0, v);
+      const int vi = M.vinfo[j0];
+      float ax = 0.f, ay = 0.f;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        float g = v[p].x;
+        if (S::delta) g += M.mabs[j0 + p].x;
+        const float4 co = M.coef[j0 + p];
+        ax = fmaf(fabsf(co.z), g, ax);
+        ay = fmaf(fabsf(co.w), g, ay);
+      }
+      if (vi_sx(vi) < 0) kahan(hs[0], cs[0], ax);
+      if (vi_sx(vi) > 0) kahan(hs[1], cs[1], ax);
+      if (vi_sy(vi) < 0) kahan(hs[2], cs[2], ay);
+      if (vi_sy(vi) > 0) kahan(hs[3], cs[3], ay);
+    }
+    float ls[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ls[k] = -cs[k];
+    float oh, ol;
+    warp_reduce4_ff(hs, ls, oh, ol);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const float th = __shfl_sync(0xffffffffu, oh, 8 * f), tl = __shfl_sync(0xffffffffu, ol, 8 * f);
+      if (diff >> f & 1u) C.nw[f] = (float)(((double)th + (double)tl) * P.dv / M.emitted[f]);
+    }
+  }
+  return C;
+}
+
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) x += __shfl_xor_sync(0xffffffffu, x, m);
+  return x;
+}
+
+// Phase 2 for one cell, one warp: moments from the float-float sums, nu and
+// the relaxation weight, FP32 Gaussians at (U, theta), two linearised
+// effective-parameter updates (A3, FP32: the reduced forms only need the
+// correction to FP32 resolution), FP64 normalisation, factors to shared
+// memory.  Also publishes the float-float sums (msum) from which bgk_moments
+// forms FP64 moments on request.
+template <int PREC>
+__device__ void cell_params_f32(const Params& P, const MixedTables& M, int cell, const float2 (*part)[4],
+                                int wpc, float* __restrict__ px, float* __restrict__ py, float* sa, float* sk,
+                                int* sok, float2* __restrict__ msum, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  float h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    h[k] = part[0][k].x;
+    l[k] = part[0][k].y;
+    for (int w = 1; w < wpc; ++w) ff_add(h[k], l[k], part[w][k].x, part[w][k].y);
+  }
+  if (lane < 4) {
+    const int k = lane;
+    msum[(size_t)cell * 4 + k] = make_float2(k == 0 ? h[0] : k == 1 ? h[1] : k == 2 ? h[2] : h[3],
+                                             k == 0 ? l[0] : k == 1 ? l[1] : k == 2 ? l[2] : l[3]);
+  }
+  float S[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (Store<PREC>::delta) ff_add(h[k], l[k], M.mabs_ff[k].x, M.mabs_ff[k].y);
+    S[k] = h[k] + l[k];
+  }
+  const float dv = (float)P.dv;
+  float n = S[0] * dv, ux = S[1] / S[0], uy = S[2] / S[0];
+  float th = (2.0f / 3.0f) * (S[3] / S[0] - (ux * ux + uy * uy));
+  bool ok = n > 0.f && th > 0.f && isfinite(n) && isfinite(ux) && isfinite(uy) && isfinite(th);
+  if (!ok) {
+    n = 1.f;
+    ux = uy = 0.f;
+    th = 1.f;
+  }
+  const float nu = n * (P.omega == 0.5 ? sqrtf(th) : powf(th, (float)(1.0 - P.omega)));
+  const float a = P.relax_exact ? 1.0f - expf(-nu * (float)P.dt) : nu * (float)P.dt;
+  // Gaussians at q, and their central sums M_m = sum d^m e
+  const float inv = 1.0f / th;
+  float Mx[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, My[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int j = lane; j < P.nvx; j += 32) {
+    const float d = M.cx[j] - ux;
+    const float e = expf(-(d * d) * inv);
+    px[j] = e;
+    float t = e;
+    Mx[0] += t;
+    t *= d;
+    Mx[1] += t;
+    t *= d;
+    Mx[2] += t;
+    t *= d;
+    Mx[3] += t;
+    t *= d;
+    Mx[4] += t;
+  }
+  for (int j = lane; j < P.nvy; j += 32) {
+    const float d = M.cy[j] - uy;
+    const float e = expf(-(d * d) * inv);
+    py[j] = e;
+    float t = e;
+    My[0] += t;
+    t *= d;
+    My[1] += t;
+    t *= d;
+    My[2] += t;
+    t *= d;
+    My[3] += t;
+    t *= d;
+    My[4] += t;
+  }
+  float p[4] = {n, ux, uy, th};
+  if (P.conservative) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      Mx[m] = warp_sum_f(Mx[m]);
+      My[m] = warp_sum_f(My[m]);
+    }
+    const float q[4] = {n, ux, uy, th};
+    for (int it = 0; it < 2; ++it) {
+      const float w2 = (p[3] - th) * inv * inv;
+      const float w1x = 2.f * (p[1] - ux) * inv, w1y = 2.f * (p[2] - uy) * inv;
+      float Sx[3], Sy[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        Sx[m] = Mx[m] + w1x * Mx[m + 1] + w2 * Mx[m + 2];
+        Sy[m] = My[m] + w1y * My[m + 1] + w2 * My[m + 2];
+      }
+      const float mux = Sx[1] / Sx[0], muy = Sy[1] / Sy[0];
+      float d[4];
+      d[0] = p[0] / (3.14159265f * p[3]) * dv * Sx[0] * Sy[0];
+      d[1] = ux + mux;
+      d[2] = uy + muy;
+      d[3] = (2.f / 3.f) * ((Sx[2] / Sx[0] - mux * mux) + (Sy[2] / Sy[0] - muy * muy) + 0.5f * p[3]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) p[k] += q[k] - d[k];
+    }
+    if (!(p[0] > 0.f) || !(p[3] > 0.f) || !isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2]) ||
+        !isfinite(p[3])) {
+      ok = false;
+    }
+  }
+  if (ok) {
+    // the Maxwellian normalisation n / (pi theta) in FP64
+    const float ap = (float)((double)a * ((double)p[0] / (kPi() * (double)p[3])));
+    const float w2 = (p[3] - th) * inv * inv;
+    const float w1x = 2.f * (p[1] - ux) * inv, w1y = 2.f * (p[2] - uy) * inv;
+    for (int j = lane; j < P.nvx; j += 32) {
+      const float d = M.cx[j] - ux;
+      px[j] = ap * (px[j] * fmaf(d, fmaf(d, w2, w1x), 1.0f));
+    }
+    for (int j = lane; j < P.nvy; j += 32) {
+      const float d = M.cy[j] - uy;
+      py[j] = py[j] * fmaf(d, fmaf(d, w2, w1y), 1.0f);
+    }
+  }
+  if (lane == 0) {
+    *sa = a;
+    *sk = 0.5f * p[3];
+    *sok = ok ? 1 : 0;
+    if (!ok) atomicOr(err, ERR_MOMENT);
+  }
+}
+
+// Stochastic rounding of an FP32 value to BF16: add 16 bits of a hash of the
+// value and its position below the kept bits, then truncate.  Unbiased, so
+// per-step updates smaller than half a BF16 ulp of the deviation survive on
+// average instead of being rounded away every step.
+__device__ __forceinline__ unsigned bf16_sr(float x, unsigned salt) {
+  const unsigned u = __float_as_uint(x);
+  unsigned h = u * 0x9E3779B1u ^ salt;
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return (u + (h & 0xFFFFu)) >> 16;
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_result(void* fout, size_t idx, const float2 (&r)[4]) {
+  if (PREC == PREC_BF16) {
+    unsigned w[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const unsigned salt = (unsigned)(idx + p) * 2u;
+      w[p] = bf16_sr(r[p].x, salt) | (bf16_sr(r[p].y, salt + 1u) << 16);
+    }
+    *reinterpret_cast<uint4*>(static_cast<unsigned*>(fout) + idx) = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    Store<PREC>::store4(fout, idx, r);
+  }
+}
+
+}  // namespace
+
+// 768 resident threads per SM at most 80 registers each.
+template <int PREC, int G, int MGL>
+__global__ void __launch_bounds__(256, 3)
+    step_mixed_kernel(const void* __restrict__ fin, void* __restrict__ fout, float2* __restrict__ msum,
+                      const Params P, const MixedTables M, int* __restrict__ err) {
+  constexpr int WPC = 8 / G;
+  extern __shared__ float4 smemf4[];
+  float* phx = reinterpret_cast<float*>(smemf4);
+  float* phy = phx + G * P.nvx;
+  __shared__ float2 s_part[G][WPC][4];
+  __shared__ float s_a[G], s_k[G];
+  __shared__ int s_ok[G];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = warp / WPC, wc = warp % WPC;
+  const int cell = blockIdx.x * G + c;
+  const bool live = cell < P.nx * P.ny;
+  const int ngroups = P.nv >> 2;
+  const int lic = wc * 32 + lane;
+
+  float2 ft[MGL][4];
+  CellCtx C;
+  if (live) {
+    C = cell_ctx<PREC>(P, M, fin, cell);
+    // A1 + A2: stream this lane's groups, float-float moment sums
+    float hs[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < MGL; ++k) {
+      const int g = lic + k * 32 * WPC;
+      if (g < ngroups) {
+        const int j0 = 4 * g;
+        stream_group<PREC>(P, M, fin, C, j0, ft[k]);
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const float4 co = M.coef[j0 + p];
+          const float c2 = fmaf(co.z, co.z, co.w * co.w);
+          p0 += ft[k][p].x;
+          p1 = fmaf(co.z, ft[k][p].x, p1);
+          p2 = fmaf(co.w, ft[k][p].x, p2);
+          p3 = fmaf(c2, ft[k][p].x, p3) + ft[k][p].y;
+        }
+        kahan(hs[0], cs[0], p0);
+        kahan(hs[1], cs[1], p1);
+        kahan(hs[2], cs[2], p2);
+        kahan(hs[3], cs[3], p3);
+      }
+    }
+    float ls[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ls[k] = -cs[k];
+    float oh, ol;
+    warp_reduce4_ff(hs, ls, oh, ol);
+    if ((lane & 7) == 0) s_part[c][wc][lane >> 3] = make_float2(oh, ol);
+  }
+  __syncthreads();
+  if (live && wc == 0)
+    cell_params_f32<PREC>(P, M, cell, s_part[c], WPC, phx + c * P.nvx, phy + c * P.nvy, &s_a[c], &s_k[c],
+                          &s_ok[c], msum, err);
+  __syncthreads();
+  if (!live) return;
+
+  // A4: f^{n+1} = f~ + (a Phi - a f~)
+  const float a = s_a[c], kappa = s_k[c];
+  const bool ok = s_ok[c] != 0;
+  const float* px = phx + c * P.nvx;
+  const float* py = phy + c * P.nvy;
+#pragma unroll
+  for (int k = 0; k < MGL; ++k) {
+    const int g = lic + k * 32 * WPC;
+    if (g < ngroups) {
+      const int j0 = 4 * g;
+      float2 r[4] = {ft[k][0], ft[k][1], ft[k][2], ft[k][3]};
+      if (ok) {
+        const int vi = M.vinfo[j0];
+        const float4 xv = *reinterpret_cast<const float4*>(px + vi_jx(vi));
+        const float yv = py[vi_jy(vi)];
+        const float ph[4] = {xv.x * yv, xv.y * yv, xv.z * yv, xv.w * yv};
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          float fg = r[p].x, fh = r[p].y;  // full f~ for the a f~ term
+          if (Store<PREC>::delta) {
+            const float2 m = M.mabs[j0 + p];
+            fg += m.x;
+            fh += m.y;
+          }
+          r[p].x += fmaf(-a, fg, ph[p]);
+          r[p].y += fmaf(-a, fh, kappa * ph[p]);
+        }
+      }
+      store_result<PREC>(fout, C.c0 + j0, r);
+    }
+  }
+}
+
+// FP64 moments (n, ux, uy, theta) from the float-float velocity sums a step
+// published (bgk_moments, which = 1, reduced precisions).
+__global__ void msum_moments_kernel(const Params P, const MixedTables M, int prec, const float2* msum,
+                                    double4_32a* mom) {
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= P.nx * P.ny) return;
+  double s[4];
+  for (int k = 0; k < 4; ++k) {
+    const float2 v = msum[(size_t)cell * 4 + k];
+    s[k] = (double)v.x + (double)v.y + (prec == PREC_BF16 ? M.mabs_sums[k] : 0.0);
+  }
+  double q[4];
+  moments_from_sums(s[0], s[1], s[2], s[3], P.dv, q);
+  mom[cell] = make_double4_32a(q[0], q[1], q[2], q[3]);
+}
+
+cudaError_t launch_msum_moments(const Params& P, int prec, const MixedTables& M, const float2* msum,
+                                double4_32a* mom, cudaStream_t stream) {
+  const int ncell = P.nx * P.ny;
+  msum_moments_kernel<<<(ncell + 255) / 256, 256, 0, stream>>>(P, M, prec, msum, mom);
+  return cudaGetLastError();
+}
+
+// ---- tables -------------------------------------------------------------------
+// FP32 copies of the per-velocity tables, the FP32 absolute Maxwellian and
+// the FP64 sums that pin the mixed form's moments and wall fluxes to the
+// values actually stored.
+__global__ void mixed_tables_kernel(const Params P, const Tables T, float4* coef, float* cx, float* cy,
+                                    float2* ghost, float2* mabs) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P.nv) return;
+  const int jx = j % P.nvx, jy = j / P.nvx;
+  const double4_32a c = T.coef[j];
+  const double2 v = T.cxy[j];
+  coef[j] = make_float4((float)c.y, (float)c.z, (float)v.x, (float)v.y);
+  if (jy == 0) cx[jx] = (float)v.x;
+  if (jx == 0) cy[jy] = (float)v.y;
+  for (int face = 0; face < kFaces; ++face) {
+    const double2 g = T.ghost[face * P.nv + j];
+    ghost[face * P.nv + j] = make_float2((float)g.x, (float)g.y);
+  }
+  const double unit[4] = {1.0, 0.0, 0.0, 1.0};
+  const double2 m = maxwell_point(P.dim, unit, v.x, v.y);
+  mabs[j] = make_float2((float)m.x, (float)m.y);
+}
+
+__global__ void __launch_bounds__(256) mixed_sums_kernel(const Params P, const MixedTables M,
+                                                         double* mabs_sums, float2* mabs_ff, double* emitted) {
+  __shared__ double red[4 * 8];
+  __shared__ double tot[4];
+  double s[4] = {0.0, 0.0, 0.0, 0.0}, e[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = threadIdx.x; j < P.nv; j += 256) {
+    const float4 co = M.coef[j];
+    const double cx = co.z, cy = co.w;
+    const double c2 = (double)fmaf(co.z, co.z, co.w * co.w);
+    const float2 m = M.mabs[j];
+    s[0] += m.x;
+    s[1] = fma(cx, (double)m.x, s[1]);
+    s[2] = fma(cy, (double)m.x, s[2]);
+    s[3] = fma(c2, (double)m.x, s[3]) + (double)m.y;
+    const double cn[4] = {cx, -cx, cy, -cy};
+    for (int f = 0; f < 4; ++f)
+      if (P.bc_kind[f] == BC_DIFFUSE && cn[f] > 0.0) e[f] = fma(cn[f], (double)M.ghost[f * P.nv + j].x, e[f]);
+  }
+  block_reduce4<256>(s[0], s[1], s[2], s[3], red, tot);
+  if (threadIdx.x < 4) {
+    const double v = tot[threadIdx.x];
+    mabs_sums[threadIdx.x] = v;
+    const float hi = (float)v;
+    mabs_ff[threadIdx.x] = make_float2(hi, (float)(v - (double)hi));
+  }
+  block_reduce4<256>(e[0], e[1], e[2], e[3], red, tot);
+  if (threadIdx.x < 4) emitted[threadIdx.x] = tot[threadIdx.x] * P.dv;
+}
+
+cudaError_t launch_build_mixed_tables(const Params& P, const Tables& T, const MixedTables& M,
+                                      cudaStream_t stream) {
+  mixed_tables_kernel<<<(P.nv + 255) / 256, 256, 0, stream>>>(
+      P, T, const_cast<float4*>(M.coef), const_cast<float*>(M.cx), const_cast<float*>(M.cy),
+      const_cast<float2*>(M.ghost), const_cast<float2*>(M.mabs));
+  mixed_sums_kernel<<<1, 256, 0, stream>>>(P, M, const_cast<double*>(M.mabs_sums),
+                                           const_cast<float2*>(M.mabs_ff), const_cast<double*>(M.emitted));
+  return cudaGetLastError();
+}
+
+// ---- conversions between the FP64 layout of the ABI and the storage ------------
+template <int PREC>
+__global__ void to_f64_kernel(const Params P, const MixedTables M, const void* f, double2* out) {
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t total = (size_t)P.nx * P.ny * P.nv;
+  if (idx >= total) return;
+  const float2 v = Store<PREC>::load1(f, idx);
+  double2 r = make_double2((double)v.x, (double)v.y);
+  if (Store<PREC>::delta) {
+    const float2 m = M.mabs[idx % P.nv];
+    r.x += (double)m.x;
+    r.y += (double)m.y;
+  }
+  out[idx] = r;
+}
+
+template <int PREC>
+__global__ void from_f64_kernel(const Params P, const MixedTables M, const double2* in, void* f) {
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t total = (size_t)P.nx * P.ny * P.nv;
+  if (idx >= total) return;
+  double2 v = in[idx];
+  if (PREC == PREC_F32) {
+    static_cast<float2*>(f)[idx] = make_float2((float)v.x, (float)v.y);
+  } else {
+    const float2 m = M.mabs[idx % P.nv];
+    v.x -= (double)m.x;
+    v.y -= (double)m.y;
+    static_cast<unsigned*>(f)[idx] = Store<PREC_BF16>::pack(make_float2((float)v.x, (float)v.y));
+  }
+}
+
+cudaError_t launch_to_f64(const Params& P, int prec, const MixedTables& M, const void* f, double2* out,
+                          cudaStream_t stream) {
+  const size_t total = (size_t)P.nx * P.ny * P.nv;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  if (prec == PREC_F32) to_f64_kernel<PREC_F32><<<grid, 256, 0, stream>>>(P, M, f, out);
+  else to_f64_kernel<PREC_BF16><<<grid, 256, 0, stream>>>(P, M, f, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_f64(const Params& P, int prec, const MixedTables& M, const double2* in, void* f,
+                            cudaStream_t stream) {
+  const size_t total = (size_t)P.nx * P.ny * P.nv;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  if (prec == PREC_F32) from_f64_kernel<PREC_F32><<<grid, 256, 0, stream>>>(P, M, in, f);
+  else from_f64_kernel<PREC_BF16><<<grid, 256, 0, stream>>>(P, M, in, f);
+  return cudaGetLastError();
+}
+
+// ---- launch ------------------------------------------------------------------
+namespace {
+
+size_t mixed_smem(const Params& P, int G) { return sizeof(float) * (size_t)G * (P.nvx + P.nvy); }
+
+template <int PREC, int G, int MGL>
+cudaError_t launch_mg(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
+                      int* err, cudaStream_t stream) {
+  const int ncell = P.nx * P.ny;
+  const unsigned grid = (unsigned)((ncell + G - 1) / G);
+  step_mixed_kernel<PREC, G, MGL><<<grid, 256, mixed_smem(P, G), stream>>>(fin, fout, msum, P, M, err);
+  return cudaGetLastError();
+}
+
+template <int PREC, int G>
+cudaError_t dispatch_mgl(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
+                         int* err, cudaStream_t stream) {
+  switch (P.mgl) {
+    case 2: return launch_mg<PREC, G, 2>(P, M, fin, fout, msum, err, stream);
+    case 4: return launch_mg<PREC, G, 4>(P, M, fin, fout, msum, err, stream);
+    case 6: return launch_mg<PREC, G, 6>(P, M, fin, fout, msum, err, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int PREC>
+cudaError_t dispatch_m(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
+                       int* err, cudaStream_t stream) {
+  switch (P.tile) {
+    case 1: return dispatch_mgl<PREC, 1>(P, M, fin, fout, msum, err, stream);
+    case 2: return dispatch_mgl<PREC, 2>(P, M, fin, fout, msum, err, stream);
+    case 4: return dispatch_mgl<PREC, 4>(P, M, fin, fout, msum, err, stream);
+    case 8: return dispatch_mgl<PREC, 8>(P, M, fin, fout, msum, err, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t step_mixed_smem_bytes(const Params& P, int tile) { return mixed_smem(P, tile); }
+
+// Groups of 4 velocities per lane when a cell has 256/tile lanes, rounded up
+// to an instantiated count (2, 4 or 6); 0 if more than 6 would be needed.
+int mixed_groups_per_lane(const Params& P, int tile) {
+  const int lanes = 256 / tile;
+  const int need = (P.nv / 4 + lanes - 1) / lanes;
+  if (need <= 2) return 2;
+  if (need <= 4) return 4;
+  if (need <= 6) return 6;
+  return 0;
+}
+
+cudaError_t prepare_step_mixed(const Params&, int) { return cudaSuccess; }
+
+cudaError_t launch_step_mixed(const Params& P, int prec, const MixedTables& M, const void* fin, void* fout,
+                              double4_32a* mom, int* err, cudaStream_t stream) {
+  float2* msum = reinterpret_cast<float2*>(mom);  // 32 bytes per cell either way
+  return prec == PREC_F32 ? dispatch_m<PREC_F32>(P, M, fin, fout, msum, err, stream)
+                          : dispatch_m<PREC_BF16>(P, M, fin, fout, msum, err, stream);
+}
+
+}  // namespace bgk

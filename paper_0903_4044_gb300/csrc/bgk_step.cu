@@ -201,13 +201,6 @@ __device__ __forceinline__ void axis_sums(const double* __restrict__ c, int n, d
   M[4] = m4;
 }
 
-// Sums of the Gaussian moved from base (u0, th0) to (u0 + du, th0 + dth), to
-// first order: e' = e (1 + d (w1 + d w2)), w1 = 2 du / th0, w2 = dth / th0^2.
-__device__ __forceinline__ void shifted(const double M[5], double w1, double w2, double out[3]) {
-#pragma unroll
-  for (int m = 0; m < 3; ++m) out[m] = M[m] + w1 * M[m + 1] + w2 * M[m + 2];
-}
-
 template <int DIM, int G>
 __device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, const double (*sums)[4],
                                  double* __restrict__ phx, double* __restrict__ phy, double* sb,
@@ -221,112 +214,56 @@ __device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, co
   bool ok = live && moments_ok(qm);
   // a failed cell keeps its lanes busy on a harmless stand-in state
   const double q[4] = {ok ? qm[0] : 1.0, ok ? qm[1] : 0.0, ok ? qm[2] : 0.0, ok ? qm[3] : 1.0};
-  // relaxation weights from nu = n theta^(1-omega)
-  double a = 0.0, b = 1.0;
-  {
-    const double nu = q[0] * (P.omega == 0.5 ? sqrt(q[3]) : pow(q[3], 1.0 - P.omega));
-    if (P.relax_exact) {
-      b = exp(-nu * P.dt);
-      a = 1.0 - b;
-    } else {
-      a = P.dt * nu;
-      b = 1.0 - a;
-    }
-  }
+  double a, b;
+  relax_weights(P, q, a, b);
   double* px = phx + c * P.nvx;
   double* py = phy + c * P.nvy;
   const bool cons = P.conservative != 0;
-  double base[4] = {q[0], q[1], q[2], q[3]};
-  double p[4] = {q[0], q[1], q[2], q[3]};
+  EffState E;
+  eff_init(E, q, !(cons && ok));
   double Mx[5], My[5] = {1.0, 0.0, 0.0, 0.0, 0.0};
-  bool conv = !(cons && ok), fail = false, reeval = false;
-  int it = 0;
-  const double vs = sqrt(q[3]);
   for (int round = 0; round <= kEffMaxIt; ++round) {
-    const bool need = round == 0 || reeval;
+    const bool need = round == 0 || E.reeval;
     if (!__any_sync(0xffffffffu, need)) break;
-    {
-      const double inv_th = 1.0 / base[3];
-      double Mt[5];
-      axis_sums<L>(T.cx, P.nvx, base[1], inv_th, sub, need, px, cons, Mt);
+    const double inv_th = 1.0 / E.base[3];
+    double Mt[5];
+    axis_sums<L>(T.cx, P.nvx, E.base[1], inv_th, sub, need, px, cons, Mt);
+    if (need)
+      for (int m = 0; m < 5; ++m) Mx[m] = Mt[m];
+    if (DIM == 2) {
+      axis_sums<L>(T.cy, P.nvy, E.base[2], inv_th, sub, need, py, cons, Mt);
       if (need)
-        for (int m = 0; m < 5; ++m) Mx[m] = Mt[m];
-      if (DIM == 2) {
-        axis_sums<L>(T.cy, P.nvy, base[2], inv_th, sub, need, py, cons, Mt);
-        if (need)
-          for (int m = 0; m < 5; ++m) My[m] = Mt[m];
-      }
+        for (int m = 0; m < 5; ++m) My[m] = Mt[m];
     }
-    reeval = false;
-    // A3: effective parameters, p <- p + (q - D(p)), D linearised about base
-    while (!conv && !fail && !reeval) {
-      ++it;
-      const double ith = 1.0 / base[3];
-      const double w2 = (p[3] - base[3]) * ith * ith;
-      double Sx[3], Sy[3] = {1.0, 0.0, 0.0};
-      shifted(Mx, 2.0 * (p[1] - base[1]) * ith, w2, Sx);
-      if (DIM == 2) shifted(My, 2.0 * (p[2] - base[2]) * ith, w2, Sy);
-      const double pref = (DIM == 1) ? p[0] / sqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
-      const double rx = 1.0 / Sx[0], ry = 1.0 / Sy[0];
-      const double mux = Sx[1] * rx, muy = Sy[1] * ry;
-      double d[4];
-      d[0] = pref * P.dv * Sx[0] * Sy[0];
-      d[1] = base[1] + mux;
-      d[2] = (DIM == 2) ? base[2] + muy : 0.0;
-      const double kappa = (DIM == 1) ? p[3] : 0.5 * p[3];
-      const double var = (Sx[2] * rx - mux * mux) + ((DIM == 2) ? (Sy[2] * ry - muy * muy) : 0.0);
-      d[3] = (2.0 / 3.0) * (var + kappa);
-      double r = 0.0;
-      for (int k = 0; k < 4; ++k) {
-        const double delta = q[k] - d[k];
-        p[k] += delta;
-        const double scale = (k == 0) ? q[0] : (k == 3) ? q[3] : vs;
-        r = fmax(r, fabs(delta) / scale);
-      }
-      if (!(p[0] > 0.0) || !(p[3] > 0.0) || !isfinite(r)) {
-        fail = true;
-      } else if (r < kEffTol) {
-        conv = true;
-      } else if (it >= kEffMaxIt) {
-        if (r < kEffFail) conv = true;
-        else fail = true;
-      }
-      if (!fail) {
-        const double drift = fmax(fmax(fabs(p[0] - base[0]) / base[0], fabs(p[3] - base[3]) / base[3]),
-                                  fmax(fabs(p[1] - base[1]), fabs(p[2] - base[2])) / sqrt(base[3]));
-        if (drift > kLinMax) {
-          for (int k = 0; k < 4; ++k) base[k] = p[k];
-          reeval = true;
-        }
-      }
-    }
+    E.reeval = false;
+    eff_iterate<DIM>(P, q, Mx, My, E);  // A3, linearised about E.base
   }
-  if (fail) ok = false;
+  if (E.fail) ok = false;
+  const double* p = E.p;
   if (ok) {
-    // A4 factors: a Phi_g = px[jx] py[jy], linearised from base to p
-    const double ith = 1.0 / base[3];
-    const double w2 = (p[3] - base[3]) * ith * ith;
-    const double w1x = 2.0 * (p[1] - base[1]) * ith, w1y = 2.0 * (p[2] - base[2]) * ith;
+    // A4 factors: a Phi_g = px[jx] py[jy], moved from E.base to p
+    double w1x, w1y, w2;
+    eff_lin(E, w1x, w1y, w2);
     const double pref = (DIM == 1) ? p[0] / sqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
     const double ap = a * pref;
     for (int j = sub; j < P.nvx; j += L) {
-      const double d = T.cx[j] - base[1];
+      const double d = T.cx[j] - E.base[1];
       px[j] = ap * (px[j] * fma(d, fma(d, w2, w1x), 1.0));
     }
     if (DIM == 2) {
       for (int j = sub; j < P.nvy; j += L) {
-        const double d = T.cy[j] - base[2];
+        const double d = T.cy[j] - E.base[2];
         py[j] = py[j] * fma(d, fma(d, w2, w1y), 1.0);
       }
     }
   }
-  if (sub == 0 && c < G) {
+  if (sub == 0) {
     sb[c] = b;
     sk[c] = (DIM == 1) ? p[3] : 0.5 * p[3];
     sok[c] = ok ? 1 : 0;
     if (live) {
       mom[cell] = make_double4_32a(qm[0], qm[1], qm[2], qm[3]);
-      if (!ok) atomicOr(err, fail ? ERR_EFFECTIVE : ERR_MOMENT);
+      if (!ok) atomicOr(err, E.fail ? ERR_EFFECTIVE : ERR_MOMENT);
     }
   }
 }

@@ -95,6 +95,7 @@ def _expect(cfg, status, text):
     (lambda c: setattr(c.bc[1], "n", 0.0), B.BGK_ERR_INVALID_ARG, "inflow needs"),
     (lambda c: setattr(c.bc[0], "uy", 0.3), B.BGK_ERR_INVALID_ARG, "uy must be 0"),
     (lambda c: setattr(c, "nvx", 5000), B.BGK_ERR_UNSUPPORTED, "exceeds"),
+    (lambda c: setattr(c, "precision", B.BGK_F32), B.BGK_ERR_UNSUPPORTED, "dim 2 only"),
 ])
 def test_shock_config_validation(L, mutate, status, text):
     cfg = _shock()
@@ -111,7 +112,10 @@ def test_shock_config_validation(L, mutate, status, text):
     (lambda c: (setattr(c.bc[0], "kind", B.BGK_BC_SPECULAR), setattr(c, "vx_min", -4.0)),
      B.BGK_ERR_INVALID_ARG, "symmetric"),
     (lambda c: (setattr(c, "nvx", 80), setattr(c, "nvy", 80)), B.BGK_ERR_UNSUPPORTED, "exceeds"),
-    (lambda c: setattr(c, "precision", B.BGK_BF16_DEV), B.BGK_ERR_UNSUPPORTED, "not built"),
+    (lambda c: (setattr(c, "precision", B.BGK_F32), setattr(c, "nvx", 30)), B.BGK_ERR_UNSUPPORTED,
+     "multiple of 8"),
+    (lambda c: (setattr(c, "precision", B.BGK_BF16_DEV), setattr(c, "vx_min", -4.0), setattr(c, "vx_max", 6.0)),
+     B.BGK_ERR_UNSUPPORTED, "change sign"),
 ])
 def test_cavity_config_validation(L, mutate, status, text):
     cfg = _cavity()
