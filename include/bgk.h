@@ -205,6 +205,37 @@ BGK_API const char* bgk_status_string(bgk_status st);
 /* BGK_ABI_VERSION of the loaded library. */
 BGK_API int bgk_abi_version(void);
 
+/* ---- batches and tuning ------------------------------------------------ */
+
+typedef struct bgk_batch bgk_batch;
+
+/* Many independent problems (any mix of sizes, velocity grids, dimensions
+ * and precisions) stepped together.  Each instance is a full solver created
+ * from cfgs[i] with its cuda_stream replaced by `cuda_stream`;
+ * bgk_batch_step advances every instance by nsteps with one CUDA-graph
+ * launch per 64 steps in which each instance is an independent branch, so
+ * the GPU runs the instances' step kernels concurrently.  Instances are
+ * reached with bgk_batch_solver for init, state, moments and wall fluxes
+ * (the batch owns them: do not bgk_destroy them).  On failure *out is NULL
+ * and the message names the failing instance. */
+BGK_API bgk_status bgk_batch_create(const bgk_config* cfgs, int count, void* cuda_stream,
+                                    bgk_batch** out);
+BGK_API bgk_status bgk_batch_solver(bgk_batch* b, int index, bgk_solver** out);
+BGK_API bgk_status bgk_batch_step(bgk_batch* b, int64_t nsteps);
+/* Wait for the batch stream; BGK_ERR_NUMERIC if any instance failed. */
+BGK_API bgk_status bgk_batch_sync(bgk_batch* b);
+BGK_API bgk_status bgk_batch_destroy(bgk_batch* b);
+
+/* Autotuner: time trial_steps steps for every admissible tile_cells value
+ * (cells per CTA: 1, 2, 4, 8) on the solver's own state, which is saved
+ * before and restored after the trials (the call allocates one temporary
+ * state copy), and keep the fastest.  *tile_out (may be NULL) receives it.
+ * Results do not depend on the tile beyond rounding order.  Synchronises. */
+BGK_API bgk_status bgk_autotune(bgk_solver* s, int trial_steps, int* tile_out);
+/* Tune every instance of a batch; instances with the same shape (dim, cells,
+ * velocity grid, precision) share one tuning run. */
+BGK_API bgk_status bgk_batch_autotune(bgk_batch* b, int trial_steps);
+
 /* One time step with no device allocation (the paper has no counterpart:
  * this entry point exists for callers, not for the method).
  *

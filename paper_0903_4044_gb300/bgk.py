@@ -27,7 +27,8 @@ EXPORTS = (
     "bgk_create", "bgk_destroy", "bgk_get_info", "bgk_init_maxwellian_step", "bgk_init_uniform",
     "bgk_set_state", "bgk_get_state", "bgk_step", "bgk_moments", "bgk_wall_fluxes", "bgk_sync",
     "bgk_rankine_hugoniot", "bgk_last_error", "bgk_status_string", "bgk_abi_version",
-    "bgk_step_noalloc",
+    "bgk_step_noalloc", "bgk_batch_create", "bgk_batch_solver", "bgk_batch_step", "bgk_batch_sync",
+    "bgk_batch_destroy", "bgk_autotune", "bgk_batch_autotune",
 )
 
 
@@ -95,6 +96,13 @@ def lib() -> ctypes.CDLL:
             "bgk_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "bgk_abi_version": ([], ctypes.c_int),
             "bgk_step_noalloc": ([ctypes.POINTER(bgk_config), _P, _P, _P], ctypes.c_int),
+            "bgk_batch_create": ([ctypes.POINTER(bgk_config), ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+            "bgk_batch_solver": ([_P, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+            "bgk_batch_step": ([_P, ctypes.c_int64], ctypes.c_int),
+            "bgk_batch_sync": ([_P], ctypes.c_int),
+            "bgk_batch_destroy": ([_P], ctypes.c_int),
+            "bgk_autotune": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "bgk_batch_autotune": ([_P, ctypes.c_int], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -222,3 +230,38 @@ def bgk_step_noalloc(cfg: bgk_config, f_in, f_out, mom_out) -> None:
     if not (da and db and dm):
         raise ValueError("bgk_step_noalloc takes device buffers only")
     _check(lib().bgk_step_noalloc(ctypes.byref(cfg), a, b, m), "bgk_step_noalloc")
+
+
+def bgk_batch_create(cfgs, stream=None) -> int:
+    arr = (bgk_config * len(cfgs))(*cfgs)
+    h = _P()
+    _check(lib().bgk_batch_create(arr, len(cfgs), stream, ctypes.byref(h)), "bgk_batch_create")
+    return h.value
+
+
+def bgk_batch_solver(b: int, index: int) -> int:
+    h = _P()
+    _check(lib().bgk_batch_solver(b, index, ctypes.byref(h)), "bgk_batch_solver")
+    return h.value
+
+
+def bgk_batch_step(b: int, nsteps: int) -> None:
+    _check(lib().bgk_batch_step(b, nsteps), "bgk_batch_step")
+
+
+def bgk_batch_sync(b: int) -> None:
+    _check(lib().bgk_batch_sync(b), "bgk_batch_sync")
+
+
+def bgk_batch_destroy(b: int) -> None:
+    _check(lib().bgk_batch_destroy(b), "bgk_batch_destroy")
+
+
+def bgk_autotune(h: int, trial_steps: int) -> int:
+    t = ctypes.c_int(0)
+    _check(lib().bgk_autotune(h, trial_steps, ctypes.byref(t)), "bgk_autotune")
+    return t.value
+
+
+def bgk_batch_autotune(b: int, trial_steps: int) -> None:
+    _check(lib().bgk_batch_autotune(b, trial_steps), "bgk_batch_autotune")

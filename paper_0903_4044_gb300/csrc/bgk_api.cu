@@ -8,9 +8,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "bgk.h"
 #include "bgk_internal.h"
@@ -71,6 +75,7 @@ struct bgk_solver {
   double* m_sums = nullptr;  // [12]: mabs sums, emitted, mabs sums as float-float pairs
   int* err = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int64_t gen = 0;  // bumped whenever captured launches become stale (tile change)
   int64_t steps_done = 0;
   int64_t device_bytes = 0;
   double max_courant = 0.0;
@@ -850,3 +855,298 @@ extern "C" bgk_status bgk_step_noalloc(const bgk_config* cfg, const double* f_in
   return BGK_OK;
   BGK_GUARD_END
 }
+
+// ---------------------------------------------------------------------------
+// Autotuner and batches.
+// ---------------------------------------------------------------------------
+namespace {
+
+bool tile_admissible(const bgk_solver* s, int t) {
+  bgk::Params P = s->P;
+  P.tile = t;
+  if (s->prec != bgk::PREC_F64 && bgk::mixed_groups_per_lane(P, t) == 0) return false;
+  return step_smem(P, s->prec, t) <= kMaxSmem;
+}
+
+cudaError_t set_tile(bgk_solver* s, int t) {
+  s->P.tile = t;
+  if (s->prec != bgk::PREC_F64) s->P.mgl = bgk::mixed_groups_per_lane(s->P, t);
+  s->cfg.tile_cells = t;
+  for (auto& g : s->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  ++s->gen;
+  return s->prec == bgk::PREC_F64 ? bgk::prepare_step_f64(s->P) : bgk::prepare_step_mixed(s->P, s->prec);
+}
+
+}  // namespace
+
+struct bgk_batch {
+  std::vector<bgk_solver*> inst;
+  cudaStream_t stream = nullptr;
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> branch;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  struct Graph {
+    std::vector<int64_t> key;  // per instance: parity and generation; then steps
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<Graph> graphs;
+};
+
+namespace {
+
+void batch_release(bgk_batch* b) {
+  if (!b) return;
+  for (auto& g : b->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto* s : b->inst) release(s);
+  for (auto st : b->branch)
+    if (st) cudaStreamDestroy(st);
+  for (auto ev : b->join)
+    if (ev) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+// The captured graph for `steps` steps from the instances' current buffers.
+bgk_status batch_graph(bgk_batch* b, int steps, cudaGraphExec_t* out) {
+  std::vector<int64_t> key;
+  for (auto* s : b->inst) {
+    key.push_back(s->cur);
+    key.push_back(s->gen);
+  }
+  key.push_back(steps);
+  for (auto& g : b->graphs)
+    if (g.key == key) {
+      *out = g.exec;
+      return BGK_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGetLastError();  // a stale error would be blamed on a launch below
+  if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error before batch capture");
+  e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "batch capture begin");
+  cudaError_t le = cudaEventRecord(b->fork, b->origin);
+  size_t bad = b->inst.size();
+  for (size_t i = 0; i < b->inst.size() && le == cudaSuccess; ++i) {
+    bad = i;
+    bgk_solver* s = b->inst[i];
+    le = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+    int buf = s->cur;
+    for (int t = 0; t < steps && le == cudaSuccess; ++t) {
+      le = enqueue_step(s, buf, b->branch[i]);
+      buf ^= 1;
+    }
+    if (le == cudaSuccess) le = cudaEventRecord(b->join[i], b->branch[i]);
+    if (le == cudaSuccess) le = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+  }
+  e = cudaStreamEndCapture(b->origin, &graph);
+  if (le != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    const bgk_solver* s = b->inst[bad < b->inst.size() ? bad : 0];
+    return fail(BGK_ERR_CUDA, "batch capture, instance %zu (dim %d, %dx%d cells, %d velocities, precision %d, "
+                "tile %d, groups %d): %s", bad, s->P.dim, s->P.nx, s->P.ny, s->P.nv, s->prec, s->P.tile,
+                s->P.mgl, cudaGetErrorString(le));
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batch capture end");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "batch graph instantiate");
+  if (b->graphs.size() >= 4) {
+    cudaGraphExecDestroy(b->graphs.front().exec);
+    b->graphs.erase(b->graphs.begin());
+  }
+  b->graphs.push_back({key, exec});
+  *out = exec;
+  return BGK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bgk_status bgk_autotune(bgk_solver* s, int trial_steps, int* tile_out) {
+  BGK_GUARD_BEGIN
+  if (!s) return fail(BGK_ERR_INVALID_ARG, "null solver");
+  if (trial_steps < 1) return fail(BGK_ERR_INVALID_ARG, "trial_steps must be >= 1");
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  const size_t bytes = s->point_bytes() * s->state_elems();
+  void* saved = nullptr;
+  cudaError_t e = cudaMalloc(&saved, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune state copy");
+  const int cur0 = s->cur;
+  const int64_t done0 = s->steps_done;
+  const int tile0 = s->P.tile;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  e = cudaMemcpyAsync(saved, s->f[cur0], bytes, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  int best = tile0;
+  float best_ms = 0.f;
+  for (int t : {1, 2, 4, 8}) {
+    if (e != cudaSuccess) break;
+    if (!tile_admissible(s, t)) continue;
+    e = set_tile(s, t);
+    int buf = cur0;
+    if (e == cudaSuccess) {  // one warm-up step, then the timed trial
+      e = enqueue_step(s, buf, s->stream);
+      buf ^= 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(t0, s->stream);
+    for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) {
+      e = enqueue_step(s, buf, s->stream);
+      buf ^= 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(t1, s->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess && (best_ms == 0.f || ms < best_ms)) {
+      best_ms = ms;
+      best = t;
+    }
+    // put the saved state back
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->f[cur0], saved, bytes, cudaMemcpyDeviceToDevice, s->stream);
+  }
+  if (e == cudaSuccess) e = set_tile(s, best);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  s->cur = cur0;
+  s->steps_done = done0;
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(saved);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  if (tile_out) *tile_out = best;
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_batch_create(const bgk_config* cfgs, int count, void* cuda_stream, bgk_batch** out) {
+  BGK_GUARD_BEGIN
+  if (!out) return fail(BGK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfgs || count < 1) return fail(BGK_ERR_INVALID_ARG, "need at least one configuration");
+  bgk_batch* b = new bgk_batch();
+  b->stream = (cudaStream_t)cuda_stream;
+  for (int i = 0; i < count; ++i) {
+    bgk_config c = cfgs[i];
+    c.cuda_stream = cuda_stream;
+    bgk_solver* s = nullptr;
+    bgk_status st = bgk_create(&c, &s);
+    if (st != BGK_OK) {
+      const std::string msg = g_last_error;
+      batch_release(b);
+      return fail(st, "instance %d: %s", i, msg.c_str());
+    }
+    b->inst.push_back(s);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->branch.push_back(st);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->join.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    bgk_status rs = cuda_fail(e, "batch streams");
+    batch_release(b);
+    return rs;
+  }
+  *out = b;
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_batch_solver(bgk_batch* b, int index, bgk_solver** out) {
+  if (!b || !out) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  if (index < 0 || index >= (int)b->inst.size())
+    return fail(BGK_ERR_INVALID_ARG, "instance %d out of range (batch of %zu)", index, b->inst.size());
+  *out = b->inst[index];
+  return BGK_OK;
+}
+
+bgk_status bgk_batch_step(bgk_batch* b, int64_t nsteps) {
+  BGK_GUARD_BEGIN
+  if (!b) return fail(BGK_ERR_INVALID_ARG, "null batch");
+  if (nsteps < 0) return fail(BGK_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return BGK_OK;
+  bgk_status st = select_device(b->inst[0]);
+  if (st != BGK_OK) return st;
+  while (nsteps > 0) {
+    const int k = (int)std::min<int64_t>(nsteps, kChunk);
+    cudaGraphExec_t exec = nullptr;
+    st = batch_graph(b, k, &exec);
+    if (st != BGK_OK) return st;
+    cudaError_t e = cudaGraphLaunch(exec, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+    for (auto* s : b->inst) {
+      s->steps_done += k;
+      if (k & 1) s->cur ^= 1;
+    }
+    nsteps -= k;
+  }
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_batch_sync(bgk_batch* b) {
+  BGK_GUARD_BEGIN
+  if (!b) return fail(BGK_ERR_INVALID_ARG, "null batch");
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    bgk_status st = bgk_sync(b->inst[i]);
+    if (st != BGK_OK) {
+      const std::string msg = g_last_error;
+      return fail(st, "instance %zu: %s", i, msg.c_str());
+    }
+  }
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_batch_destroy(bgk_batch* b) {
+  if (!b) return BGK_OK;
+  BGK_GUARD_BEGIN
+  cudaSetDevice(b->inst[0]->device);
+  cudaStreamSynchronize(b->stream);
+  batch_release(b);
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk_batch_autotune(bgk_batch* b, int trial_steps) {
+  BGK_GUARD_BEGIN
+  if (!b) return fail(BGK_ERR_INVALID_ARG, "null batch");
+  std::map<std::tuple<int, int, int, int, int, int>, int> known;
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    bgk_solver* s = b->inst[i];
+    const auto key = std::make_tuple(s->P.dim, s->P.nx, s->P.ny, s->P.nvx, s->P.nvy, s->prec);
+    auto it = known.find(key);
+    if (it != known.end()) {
+      cudaError_t e = set_tile(s, it->second);
+      if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+      continue;
+    }
+    int best = 0;
+    bgk_status st = bgk_autotune(s, trial_steps, &best);
+    if (st != BGK_OK) {
+      const std::string msg = g_last_error;
+      return fail(st, "instance %zu: %s", i, msg.c_str());
+    }
+    known[key] = best;
+  }
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+}  // extern "C"

@@ -333,10 +333,13 @@ cudaError_t launch_g(const Params& P, const Tables& T, const double2* fin, doubl
   return cudaGetLastError();
 }
 
+// The attribute belongs to the kernel, not to a solver: set it to the
+// largest dynamic shared memory any solver may request (226 KB) so that
+// solvers with different grids sharing an instantiation never shrink it.
 template <int DIM, int G>
-cudaError_t prepare_g(const Params& P) {
+cudaError_t prepare_g(const Params&) {
   return cudaFuncSetAttribute(step_f64_kernel<DIM, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)step_smem(P, G));
+                              226 * 1024);
 }
 
 template <int DIM>

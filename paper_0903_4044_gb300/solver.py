@@ -128,3 +128,68 @@ def make_cavity(w: dict, xi=None, stream=None, **over) -> Solver:
     s = Solver(cavity_config(**p, stream=stream))
     s.init_uniform((1.0, 0.0, 0.0, 1.0), xi, p.get("amp", 0.0) if xi is not None else 0.0)
     return s
+
+
+PRECISIONS = {"f64": B.BGK_F64, "f32": B.BGK_F32, "bf16": B.BGK_BF16_DEV}
+
+
+def instance_config(w: dict, stream=None):
+    """bgk_config of one raw workload entry (cavity or shock), with its precision."""
+    prec = PRECISIONS[w.get("precision", "f64")] if isinstance(w.get("precision"), str) else w.get("precision", 0)
+    p = {**w, "precision": prec}
+    if w["kind"] == "shock":
+        return shock_config(**p, stream=stream)[0]
+    return cavity_config(**p, stream=stream)
+
+
+class Batch:
+    """Owns a bgk_batch of instances built from raw workload entries and
+    initialised like make_shock / make_cavity (cavities perturbed from their
+    own seeds)."""
+
+    def __init__(self, ws: list[dict], stream=None, perturb=True):
+        from . import workloads as W
+
+        self.ws = ws
+        self.cfgs = [instance_config(w, stream) for w in ws]
+        self.h = B.bgk_batch_create(self.cfgs, stream)
+        self.solvers = []
+        for i, w in enumerate(ws):
+            s = Solver.__new__(Solver)
+            s.cfg = self.cfgs[i]
+            s.h = B.bgk_batch_solver(self.h, i)
+            s.info = B.bgk_get_info(s.h)
+            s.ncell, s.nv = int(s.info.ncell), int(s.info.nv)
+            s.close = lambda: None          # owned by the batch
+            if w["kind"] == "shock":
+                up, down = B.bgk_rankine_hugoniot(w["mach"], GAMMA)
+                s.init_step(0.0, up, down)
+            else:
+                xi = W.perturbation(w.get("seed", 0), s.ncell, s.nv) if perturb else None
+                s.init_uniform((1.0, 0.0, 0.0, 1.0), xi, w.get("amp", 0.0) if perturb else 0.0)
+            self.solvers.append(s)
+
+    def step(self, n: int) -> None:
+        B.bgk_batch_step(self.h, n)
+
+    def sync(self) -> None:
+        B.bgk_batch_sync(self.h)
+
+    def autotune(self, trial_steps: int = 4) -> None:
+        B.bgk_batch_autotune(self.h, trial_steps)
+        for s in self.solvers:
+            s.info = B.bgk_get_info(s.h)
+
+    def points(self) -> int:
+        return sum(s.ncell * s.nv for s in self.solvers)
+
+    def close(self) -> None:
+        if self.h:
+            B.bgk_batch_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

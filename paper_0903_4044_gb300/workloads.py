@@ -71,3 +71,32 @@ def scaled(w: dict, **over) -> dict:
     d = dict(w)
     d.update(over)
     return d
+
+
+def batch_instances(seed: int = 0, cavities: int = 64, shocks: int = 16) -> list[dict]:
+    """Raw parameters of the batched workload: `cavities` lid-driven cavities
+    with side cells from {32, 64, 96, 128, 192}, velocity grids from
+    {24, 32, 40, 48}^2 on [-5, 5]^2, Kn log-uniform in [0.01, 1] and lid Mach
+    log-uniform in [0.02, 0.3], FP32 state; then `shocks` normal shocks with
+    Mach uniform in [1.2, 5], cells uniform in [100, 800] on 40 mean free
+    paths, and a velocity box [-V, V] with V = 4 + 3 Mach cut into
+    8 round(V / 1.2) cells (about 0.3 thermal speeds each)."""
+    u = (uniform_pm1(seed, 4 * cavities + 2 * shocks) + 1.0) * 0.5  # [0, 1)
+    out = []
+    sides, grids = (32, 64, 96, 128, 192), (24, 32, 40, 48)
+    for i in range(cavities):
+        a, b, c, d = u[4 * i: 4 * i + 4]
+        out.append(dict(
+            name=f"batch_cavity_{i}", kind="cavity", n=sides[int(a * 5)], nv=grids[int(b * 4)],
+            kn=float(10.0 ** (-2.0 + 2.0 * c)),
+            lid_mach=float(10.0 ** (np.log10(0.02) + (np.log10(0.3) - np.log10(0.02)) * d)),
+            vbox=(-5.0, 5.0), omega=0.5, cfl=0.5, seed=seed + 1 + i, amp=1e-3, precision="f32"))
+    base = 4 * cavities
+    for k in range(shocks):
+        a, b = u[base + 2 * k: base + 2 * k + 2]
+        mach = float(1.2 + 3.8 * a)
+        v = 4.0 + 3.0 * mach
+        out.append(dict(
+            name=f"batch_shock_{k}", kind="shock", mach=mach, nx=min(800, int(100 + 701 * b)),
+            length=40.0, nvx=8 * int(round(v / 1.2)), vx=(-v, v), omega=0.5, cfl=0.5, precision="f64"))
+    return out

@@ -1,0 +1,96 @@
+"""Batches of uneven instances in one graph launch, and the autotuner."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0903_4044_gb300 import bgk as B
+from paper_0903_4044_gb300 import build, solver
+from paper_0903_4044_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    oracle.build()
+    B.lib()
+
+
+MIX = [
+    W.scaled(W.CAVITY_64, name="c0", n=12, nv=16, precision="f64"),
+    W.scaled(W.CAVITY_64, name="c1", n=17, nv=24, precision="f32", seed=5),
+    W.scaled(W.SHOCK_M2, name="s0", nx=40, precision="f64"),
+    W.scaled(W.CAVITY_64, name="c2", n=9, nv=32, precision="bf16", seed=7),
+]
+
+
+def _single(w):
+    cfg = solver.instance_config(w)
+    s = solver.Solver(cfg)
+    if w["kind"] == "shock":
+        up, down = B.bgk_rankine_hugoniot(w["mach"])
+        s.init_step(0.0, up, down)
+    else:
+        s.init_uniform((1.0, 0.0, 0.0, 1.0), W.perturbation(w["seed"], s.ncell, s.nv), w["amp"])
+    return s
+
+
+def test_batch_equals_independent_solvers():
+    # 70 steps = one 64-step graph + a 6-step graph; every instance must come
+    # out bit for bit as when stepped alone.
+    b = solver.Batch(MIX)
+    b.step(70)
+    b.sync()
+    for w, sb in zip(MIX, b.solvers):
+        s = _single(w)
+        s.step(70)
+        assert np.array_equal(sb.get_state(), s.get_state()), w["name"]
+        assert np.array_equal(sb.moments(which=1), s.moments(which=1)), w["name"]
+        s.close()
+    b.close()
+
+
+def test_batch_instance_error_names_instance():
+    bad = [MIX[0], W.scaled(MIX[0], nv=90)]
+    with pytest.raises(B.BgkError) as e:
+        solver.Batch(bad)
+    assert "instance 1" in str(e.value)
+
+
+def test_autotune_restores_state_and_keeps_parity():
+    w = W.scaled(W.CAVITY_64, n=20, nv=24)
+    prob0, _, _ = oracle.cavity_problem(**w)
+    xi = W.perturbation(0, prob0.ncell, prob0.nv)
+    prob, g, h = oracle.cavity_problem(**w, xi=xi)
+    s = solver.make_cavity(w, xi=xi)
+    s.step(5)
+    before = s.get_state()
+    tile = B.bgk_autotune(s.h, 3)
+    assert tile in (1, 2, 4, 8)
+    assert B.bgk_get_info(s.h).tile_cells == tile
+    assert np.array_equal(s.get_state(), before)      # trials leave no trace
+    s.step(20)
+    g1, h1, _ = oracle.step(prob, g, h, 25)
+    st = s.get_state()
+    assert np.abs(st[..., 0] - g1).max() / np.abs(g1).max() < 1e-12
+    s.close()
+
+
+def test_batch_autotune_then_step():
+    b = solver.Batch(MIX)
+    b.autotune(2)
+    b.step(9)
+    b.sync()
+    # the FP64 cavity instance against the oracle
+    w = MIX[0]
+    prob0, _, _ = oracle.cavity_problem(**w)
+    xi = W.perturbation(w["seed"], prob0.ncell, prob0.nv)
+    prob, g, h = oracle.cavity_problem(**w, xi=xi)
+    g1, h1, _ = oracle.step(prob, g, h, 9)
+    st = b.solvers[0].get_state()
+    assert np.abs(st[..., 0] - g1).max() / np.abs(g1).max() < 1e-12
+    b.close()
