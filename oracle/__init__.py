@@ -95,6 +95,9 @@ def lib():
         L.orc_step.argtypes = [_C, _D, _D, ctypes.c_long, _D]
         L.orc_wall_fluxes.argtypes = [_C, _D, _D, ctypes.c_int, _D, _D, _D, _D]
         L.orc_threads.argtypes = []
+        L.orc_lid_shear.argtypes = [_C, _D, _D]
+        L.orc_lid_shear.restype = ctypes.c_double
+        L.orc_adjoint_lid_shear.argtypes = [_C, _D, _D, ctypes.c_long, _D, _D, _D]
         _lib = L
     return _lib
 
@@ -251,6 +254,22 @@ def wall_fluxes(prob: Problem, g, h, face: int):
     if rc != 0:
         raise RuntimeError("oracle wall fluxes failed")
     return out
+
+
+def lid_shear(prob: Problem, g, h) -> float:
+    """Objective of the adjoint: lid-integrated shear of the state."""
+    return lib().orc_lid_shear(ctypes.byref(prob.cfg), _p(g), _p(h))
+
+
+def adjoint_lid_shear(prob: Problem, g, h, nsteps: int):
+    """CPU reverse pass: (J, dJ/dlnL, dJ/dU_W, dJ/dg0, dJ/dh0) after nsteps."""
+    dg, dh = prob.zeros()
+    out = np.zeros(3)
+    rc = lib().orc_adjoint_lid_shear(ctypes.byref(prob.cfg), _p(np.ascontiguousarray(g)),
+                                     _p(np.ascontiguousarray(h)), nsteps, _p(dg), _p(dh), _p(out))
+    if rc != 0:
+        raise RuntimeError("oracle adjoint failed")
+    return out[0], out[1], out[2], dg, dh
 
 
 def threads() -> int:

@@ -543,3 +543,234 @@ int orc_wall_fluxes(const orc_config* c, const double* g, const double* h, int f
   orc_bnd_free(&b);
   return 0;
 }
+
+/* ======================================================================== */
+/* Adjoint of the split step for the lid-integrated shear (2D cavity).      */
+/* ======================================================================== */
+
+/* J = sum_k dx tau_k over the face cells of YHI (inward normal -y, tangent
+ * c_x): tau_k = dV [ sum_{c_y>0} c_x (-c_y) g_k + sum_{c_y<0} c_x (-c_y) n_W G_W ]. */
+double orc_lid_shear(const orc_config* c, const double* g, const double* h) {
+  const int nf = c->nx;
+  double* m = (double*)malloc(sizeof(double) * nf * 4);
+  orc_wall_fluxes(c, g, h, ORC_YHI, m, m + nf, m + 2 * nf, m + 3 * nf);
+  double J = 0.0;
+  for (int k = 0; k < nf; ++k) J += orc_dx(c) * m[nf + k];
+  free(m);
+  return J;
+}
+
+/* Unit wall Maxwellian of a face and its derivative in the wall's x speed. */
+static void orc_wall_unit(const orc_config* c, int face, double* G, double* H, double* dG, double* dH) {
+  const double* s = c->bc_state[face];
+  const double unit[4] = {1.0, s[1], s[2], s[3]};
+  orc_maxwellian(c, unit, G, H);
+  for (int j = 0; j < orc_nv(c); ++j) {
+    const double cx = orc_cx(c, j % c->nvx);
+    dG[j] = G[j] * 2.0 * (cx - s[1]) / s[3];
+    dH[j] = 0.5 * s[3] * dG[j];
+  }
+}
+
+int orc_adjoint_lid_shear(const orc_config* c, const double* g0, const double* h0, long nsteps,
+                          double* dg0, double* dh0, double out[3]) {
+  if (c->dim != 2 || !c->relax_exact || c->bc_kind[ORC_YHI] != ORC_BC_DIFFUSE) return -1;
+  const int nv = orc_nv(c), ncell = orc_ncell(c), nx = c->nx, ny = c->ny;
+  const size_t sz = (size_t)ncell * nv;
+  const double dv = orc_dv(c), dt = c->dt, dx = orc_dx(c), dy = orc_dy(c);
+  double* Gs = (double*)malloc(sizeof(double) * sz * (nsteps + 1));
+  double* Hs = (double*)malloc(sizeof(double) * sz * (nsteps + 1));
+  memcpy(Gs, g0, sizeof(double) * sz);
+  memcpy(Hs, h0, sizeof(double) * sz);
+  for (long n = 0; n < nsteps; ++n) {
+    double* gn = Gs + sz * n;
+    double* hn = Hs + sz * n;
+    if (orc_stream(c, gn, hn, gn + sz, hn + sz) != 0 || orc_relax(c, gn + sz, hn + sz, NULL) != 0) {
+      free(Gs);
+      free(Hs);
+      return -1;
+    }
+  }
+  const double* gN = Gs + sz * nsteps;
+  const double* hN = Hs + sz * nsteps;
+
+  /* lid tables: unit wall Maxwellian, its U_W derivative, emitted flux */
+  double *GW = malloc(sizeof(double) * nv), *HW = malloc(sizeof(double) * nv);
+  double *dGW = malloc(sizeof(double) * nv), *dHW = malloc(sizeof(double) * nv);
+  orc_wall_unit(c, ORC_YHI, GW, HW, dGW, dHW);
+  double emit = 0.0, demit = 0.0, shear_w = 0.0, dshear_w = 0.0;
+  for (int j = 0; j < nv; ++j) {
+    const double cn = orc_cn(c, ORC_YHI, j), ct = orc_ct(c, ORC_YHI, j);
+    if (cn > 0.0) {
+      emit += cn * GW[j] * dv;
+      demit += cn * dGW[j] * dv;
+      shear_w += ct * cn * GW[j] * dv;
+      dshear_w += ct * cn * dGW[j] * dv;
+    }
+  }
+
+  /* objective and its explicit derivatives */
+  const double J = orc_lid_shear(c, gN, hN);
+  double dlnL = J, dUW = 0.0;
+  double* lg = (double*)calloc(sz, sizeof(double));
+  double* lh = (double*)calloc(sz, sizeof(double));
+  for (int k = 0; k < nx; ++k) {
+    const size_t cell = (size_t)(ny - 1) * nx + k;
+    double inc = 0.0;
+    for (int j = 0; j < nv; ++j) {
+      const double cn = orc_cn(c, ORC_YHI, j);
+      if (cn < 0.0) inc += -cn * gN[cell * nv + j] * dv;
+    }
+    const double nw = inc / emit;
+    dUW += dx * nw * (dshear_w - shear_w * demit / emit);
+    for (int j = 0; j < nv; ++j) {
+      const double cn = orc_cn(c, ORC_YHI, j), ct = orc_ct(c, ORC_YHI, j);
+      if (cn < 0.0) lg[cell * nv + j] = dx * (ct * cn * dv + shear_w * (-cn) * dv / emit);
+    }
+  }
+
+  /* reverse sweep */
+  double* ltg = (double*)malloc(sizeof(double) * sz);  /* adjoint of f~ */
+  double* lth = (double*)malloc(sizeof(double) * sz);
+  double* ng = (double*)malloc(sizeof(double) * sz);
+  double* nh = (double*)malloc(sizeof(double) * sz);
+  double* ftg = (double*)malloc(sizeof(double) * sz);
+  double* fth = (double*)malloc(sizeof(double) * sz);
+  double* G = (double*)malloc(sizeof(double) * nv);
+  double* H = (double*)malloc(sizeof(double) * nv);
+  double* Gf[4], *Hf[4], *dGf[4], *dHf[4];
+  double emitf[4] = {0, 0, 0, 0};
+  for (int f = 0; f < 4; ++f) {
+    Gf[f] = malloc(sizeof(double) * nv);
+    Hf[f] = malloc(sizeof(double) * nv);
+    dGf[f] = malloc(sizeof(double) * nv);
+    dHf[f] = malloc(sizeof(double) * nv);
+    orc_wall_unit(c, f, Gf[f], Hf[f], dGf[f], dHf[f]);
+    for (int j = 0; j < nv; ++j)
+      if (orc_cn(c, f, j) > 0.0) emitf[f] += orc_cn(c, f, j) * Gf[f][j] * dv;
+  }
+  int rc = 0;
+  for (long n = nsteps - 1; n >= 0 && rc == 0; --n) {
+    const double* gn = Gs + sz * n;
+    const double* hn = Hs + sz * n;
+    orc_stream(c, gn, hn, ftg, fth);
+    /* collision adjoint, cell by cell (Eq. relaxation differentiated) */
+    for (int cell = 0; cell < ncell; ++cell) {
+      const double* gt = ftg + (size_t)cell * nv;
+      const double* ht = fth + (size_t)cell * nv;
+      double q[4], p[4];
+      orc_moments(c, gt, ht, q);
+      for (int k = 0; k < 4; ++k) p[k] = q[k];
+      if (c->conservative && orc_effective_params(c, q, p) < 0) {
+        rc = -1;
+        break;
+      }
+      orc_maxwellian(c, p, G, H);
+      const double nu = q[0] * pow(q[3], 1.0 - c->omega);
+      const double e = exp(-nu * dt);
+      const double a = 1.0 - e;
+      const double* lgc = lg + (size_t)cell * nv;
+      const double* lhc = lh + (size_t)cell * nv;
+      double sa = 0.0, sp[4] = {0, 0, 0, 0};
+      double E = 0.0;
+      for (int j = 0; j < nv; ++j) {
+        const double cx = orc_cx(c, j % c->nvx), cy = orc_cy(c, j / c->nvx);
+        E += ((cx * cx + cy * cy) * gt[j] + ht[j]) * dv;
+        sa += lgc[j] * (G[j] - gt[j]) + lhc[j] * (H[j] - ht[j]);
+        const double dxp = cx - p[1], dyp = cy - p[2];
+        const double dG[4] = {G[j] / p[0], G[j] * 2.0 * dxp / p[3], G[j] * 2.0 * dyp / p[3],
+                              G[j] * ((dxp * dxp + dyp * dyp) / (p[3] * p[3]) - 1.0 / p[3])};
+        for (int k = 0; k < 4; ++k) {
+          const double dH = 0.5 * p[3] * dG[k] + (k == 3 ? 0.5 * G[j] : 0.0);
+          sp[k] += lgc[j] * dG[k] + lhc[j] * dH;
+        }
+      }
+      /* adjoint of q: Phi through p (dp/dq = identity), a through nu */
+      const double da_dn = dt * e * pow(q[3], 1.0 - c->omega);
+      const double da_dth = dt * e * (1.0 - c->omega) * q[0] * pow(q[3], -c->omega);
+      const double mu[4] = {a * sp[0] + da_dn * sa, a * sp[1], a * sp[2], a * sp[3] + da_dth * sa};
+      dlnL += sa * nu * dt * e; /* dt scales with L */
+      const double n_ = q[0], ux = q[1], uy = q[2];
+      for (int j = 0; j < nv; ++j) {
+        const double cx = orc_cx(c, j % c->nvx), cy = orc_cy(c, j / c->nvx);
+        const double dn = dv;
+        const double dux = dv * (cx - ux) / n_;
+        const double duy = dv * (cy - uy) / n_;
+        const double dth = (2.0 / 3.0) * (dv / n_) * ((cx * cx + cy * cy) - E / n_ - 2.0 * (ux * (cx - ux) + uy * (cy - uy)));
+        ltg[(size_t)cell * nv + j] = (1.0 - a) * lgc[j] + mu[0] * dn + mu[1] * dux + mu[2] * duy + mu[3] * dth;
+        lth[(size_t)cell * nv + j] = (1.0 - a) * lhc[j] + mu[3] * (2.0 / 3.0) * dv / n_;
+      }
+    }
+    if (rc) break;
+    /* streaming adjoint: scatter each f~ back to its sources (transposed
+       donor cell); boundary sources feed the wall density n_W */
+    memset(ng, 0, sizeof(double) * sz);
+    memset(nh, 0, sizeof(double) * sz);
+    for (int cell = 0; cell < ncell; ++cell) {
+      const int ix = cell % nx, iy = cell / nx;
+      double lam_face[4] = {0, 0, 0, 0};
+      double inc[4] = {0, 0, 0, 0};
+      for (int j = 0; j < nv; ++j) {
+        for (int f = 0; f < 4; ++f)
+          if (orc_cn(c, f, j) < 0.0) inc[f] += -orc_cn(c, f, j) * gn[(size_t)cell * nv + j] * dv;
+      }
+      for (int j = 0; j < nv; ++j) {
+        const double cx = orc_cx(c, j % c->nvx), cy = orc_cy(c, j / c->nvx);
+        const double ax = fabs(cx) * dt / dx, ay = fabs(cy) * dt / dy;
+        const size_t id = (size_t)cell * nv + j;
+        ng[id] += (1.0 - ax - ay) * ltg[id];
+        nh[id] += (1.0 - ax - ay) * lth[id];
+        for (int axis = 0; axis < 2; ++axis) {
+          const double cc = axis == 0 ? cx : cy, w = axis == 0 ? ax : ay;
+          if (cc == 0.0) continue;
+          const int sx = axis == 0 ? (cc > 0.0 ? -1 : 1) : 0, sy = axis == 1 ? (cc > 0.0 ? -1 : 1) : 0;
+          const int jx2 = ix + sx, iy2 = iy + sy;
+          if (jx2 >= 0 && jx2 < nx && iy2 >= 0 && iy2 < ny) {
+            const size_t src = ((size_t)iy2 * nx + jx2) * nv + j;
+            ng[src] += w * ltg[id];
+            nh[src] += w * lth[id];
+          } else {
+            const int face = axis == 0 ? (cc > 0.0 ? ORC_XLO : ORC_XHI) : (cc > 0.0 ? ORC_YLO : ORC_YHI);
+            if (c->bc_kind[face] == ORC_BC_DIFFUSE) {
+              lam_face[face] += w * (ltg[id] * Gf[face][j] + lth[id] * Hf[face][j]);
+              if (face == ORC_YHI) {
+                const double nw = inc[face] / emitf[face];
+                const double dgh = nw * (dGf[face][j] - Gf[face][j] * demit / emitf[face]);
+                const double dhh = nw * (dHf[face][j] - Hf[face][j] * demit / emitf[face]);
+                dUW += w * (ltg[id] * dgh + lth[id] * dhh);
+              }
+            } else if (c->bc_kind[face] == ORC_BC_SPECULAR) {
+              const size_t src = (size_t)cell * nv + orc_reflect(c, face, j);
+              ng[src] += w * ltg[id];
+              nh[src] += w * lth[id];
+            }
+          }
+        }
+      }
+      /* n_W = dv sum_{c_n<0} |c_n| g / emitted */
+      for (int f = 0; f < 4; ++f) {
+        if (lam_face[f] == 0.0) continue;
+        for (int j = 0; j < nv; ++j)
+          if (orc_cn(c, f, j) < 0.0) ng[(size_t)cell * nv + j] += lam_face[f] * (-orc_cn(c, f, j)) * dv / emitf[f];
+      }
+    }
+    memcpy(lg, ng, sizeof(double) * sz);
+    memcpy(lh, nh, sizeof(double) * sz);
+  }
+  if (rc == 0) {
+    memcpy(dg0, lg, sizeof(double) * sz);
+    memcpy(dh0, lh, sizeof(double) * sz);
+    out[0] = J;
+    out[1] = dlnL;
+    out[2] = dUW;
+  }
+  for (int f = 0; f < 4; ++f) {
+    free(Gf[f]);
+    free(Hf[f]);
+    free(dGf[f]);
+    free(dHf[f]);
+  }
+  free(G); free(H); free(ftg); free(fth); free(ng); free(nh); free(ltg); free(lth);
+  free(lg); free(lh); free(GW); free(HW); free(dGW); free(dHW); free(Gs); free(Hs);
+  return rc;
+}

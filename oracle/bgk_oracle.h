@@ -102,6 +102,21 @@ int orc_wall_fluxes(const orc_config* c, const double* g, const double* h, int f
 /* Threads used by the OpenMP loops over cells (1 when built without it). */
 int orc_threads(void);
 
+/* Objective of the adjoint: the lid-integrated shear J = sum over the cells
+ * of face YHI of dx * tau_k, tau_k the shear flux of orc_wall_fluxes (the
+ * drag of Sec. 5.2 up to its normalisation). */
+double orc_lid_shear(const orc_config* c, const double* g, const double* h);
+
+/* Reverse pass of nsteps split steps (2D, exact relaxation) from (g0, h0):
+ * out = {J, dJ/d ln L, dJ/dU_W} and dJ/dg0, dJ/dh0 (same layout as g, h).
+ * L scales the domain and, through the Courant rule, the time step together
+ * (Kn = 1/L for the cavity); U_W is the x velocity of face YHI.  The
+ * effective-parameter map p(q) is linearised by the identity (its Jacobian
+ * differs from it by the quadrature residual).  Stores every state.
+ * Returns 0, or -1 on an unsupported configuration or a failed step. */
+int orc_adjoint_lid_shear(const orc_config* c, const double* g0, const double* h0, long nsteps,
+                          double* dg0, double* dh0, double out[3]);
+
 #ifdef __cplusplus
 }
 #endif
