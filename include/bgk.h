@@ -236,6 +236,27 @@ BGK_API bgk_status bgk_autotune(bgk_solver* s, int trial_steps, int* tile_out);
  * velocity grid, precision) share one tuning run. */
 BGK_API bgk_status bgk_batch_autotune(bgk_batch* b, int trial_steps);
 
+/* ---- adjoint -------------------------------------------------------------- */
+
+/* Gradient of the lid-integrated shear by the adjoint of the split step.
+ * J = sum over the cells of face YHI of dx * tau_k, tau_k the shear flux of
+ * bgk_wall_fluxes (the drag of Sec. 5.2 up to its normalisation), after
+ * nsteps steps from the solver's current state f0.  Runs the steps forward
+ * (saving the state every checkpoint_every steps), then backward segment by
+ * segment, recomputing each segment's states from its checkpoint: device
+ * memory of about (nsteps / checkpoint_every + checkpoint_every + 3) states.
+ * Outputs: out = {J, dJ/d ln L, dJ/dU_W}, where L scales the domain and,
+ * through the Courant rule, the time step together (Kn = 1/L for the
+ * cavity: dJ/dKn = -(dJ/d ln L)/Kn) and U_W is the lid's (YHI) x speed;
+ * dJ_df0 (STATE LAYOUT, host or device per on_device; may be NULL) receives
+ * dJ/df0.  The map from moments to effective Maxwellian parameters is
+ * linearised by the identity (exact up to the quadrature residual of the
+ * velocity grid).  On return the solver holds the state after nsteps.
+ * Requires dim 2, BGK_F64, exact relaxation, a diffuse lid (YHI) and a time
+ * step derived from cfl (dt = 0).  Synchronises; allocates its buffers. */
+BGK_API bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int checkpoint_every, double* dJ_df0,
+                                         int on_device, double out[3]);
+
 /* One time step with no device allocation (the paper has no counterpart:
  * this entry point exists for callers, not for the method).
  *

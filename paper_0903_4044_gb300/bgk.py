@@ -28,7 +28,7 @@ EXPORTS = (
     "bgk_set_state", "bgk_get_state", "bgk_step", "bgk_moments", "bgk_wall_fluxes", "bgk_sync",
     "bgk_rankine_hugoniot", "bgk_last_error", "bgk_status_string", "bgk_abi_version",
     "bgk_step_noalloc", "bgk_batch_create", "bgk_batch_solver", "bgk_batch_step", "bgk_batch_sync",
-    "bgk_batch_destroy", "bgk_autotune", "bgk_batch_autotune",
+    "bgk_batch_destroy", "bgk_autotune", "bgk_batch_autotune", "bgk_adjoint_lid_shear",
 )
 
 
@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
             "bgk_batch_destroy": ([_P], ctypes.c_int),
             "bgk_autotune": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "bgk_batch_autotune": ([_P, ctypes.c_int], ctypes.c_int),
+            "bgk_adjoint_lid_shear": ([_P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int, _D4], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -265,3 +266,11 @@ def bgk_autotune(h: int, trial_steps: int) -> int:
 
 def bgk_batch_autotune(b: int, trial_steps: int) -> None:
     _check(lib().bgk_batch_autotune(b, trial_steps), "bgk_batch_autotune")
+
+
+def bgk_adjoint_lid_shear(h: int, nsteps: int, checkpoint_every: int, grad_out=None):
+    """(J, dJ/dlnL, dJ/dU_W); dJ/df0 into grad_out (host array or CUDA tensor) if given."""
+    out = _D4()
+    addr, dev = _ptr(grad_out) if grad_out is not None else (None, 0)
+    _check(lib().bgk_adjoint_lid_shear(h, nsteps, checkpoint_every, addr, dev, out), "bgk_adjoint_lid_shear")
+    return out[0], out[1], out[2]

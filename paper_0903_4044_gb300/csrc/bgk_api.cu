@@ -1150,3 +1150,108 @@ bgk_status bgk_batch_autotune(bgk_batch* b, int trial_steps) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Adjoint driver (kernels in bgk_adjoint.cu).
+// ---------------------------------------------------------------------------
+extern "C" bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int checkpoint_every, double* dJ_df0,
+                                            int on_device, double out[3]) {
+  BGK_GUARD_BEGIN
+  if (!s || !out) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  if (nsteps < 1 || checkpoint_every < 1) return fail(BGK_ERR_INVALID_ARG, "nsteps and checkpoint_every must be >= 1");
+  if (s->P.dim != 2 || s->prec != bgk::PREC_F64 || !s->P.relax_exact)
+    return fail(BGK_ERR_UNSUPPORTED, "the adjoint needs dim 2, BGK_F64 and exact relaxation");
+  if (s->P.bc_kind[bgk::YHI] != BGK_BC_DIFFUSE) return fail(BGK_ERR_UNSUPPORTED, "the adjoint needs a diffuse lid (YHI)");
+  if (s->cfg.dt != 0.0) return fail(BGK_ERR_UNSUPPORTED, "the adjoint needs dt derived from cfl (dt = 0)");
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  const bgk::Params& P = s->P;
+  const bgk::Tables T = s->tables();
+  const size_t elems = s->state_elems(), sbytes = sizeof(double2) * elems;
+  const int K = (int)std::min<int64_t>(checkpoint_every, nsteps);
+  const int64_t M = (nsteps + K - 1) / K;
+  const int ncell = P.nx * P.ny;
+  std::vector<void*> bufs;
+  auto alloc = [&](size_t bytes, void** p) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) bufs.push_back(*p);
+    return e;
+  };
+  auto cleanup = [&]() {
+    for (void* b : bufs) cudaFree(b);
+  };
+  double2 *ckpt = nullptr, *seg = nullptr, *lam0 = nullptr, *lam1 = nullptr, *lamt = nullptr, *dghost = nullptr;
+  double *dlnl = nullptr, *duw = nullptr, *Jk = nullptr, *duw0 = nullptr, *demit = nullptr;
+  cudaError_t e = alloc(sbytes * M, (void**)&ckpt);
+  if (e == cudaSuccess) e = alloc(sbytes * K, (void**)&seg);
+  if (e == cudaSuccess) e = alloc(sbytes, (void**)&lam0);
+  if (e == cudaSuccess) e = alloc(sbytes, (void**)&lam1);
+  if (e == cudaSuccess) e = alloc(sbytes, (void**)&lamt);
+  if (e == cudaSuccess) e = alloc(sizeof(double2) * P.nv, (void**)&dghost);
+  if (e == cudaSuccess) e = alloc(sizeof(double) * ncell, (void**)&dlnl);
+  if (e == cudaSuccess) e = alloc(sizeof(double) * P.nx, (void**)&duw);
+  if (e == cudaSuccess) e = alloc(sizeof(double) * P.nx, (void**)&Jk);
+  if (e == cudaSuccess) e = alloc(sizeof(double) * P.nx, (void**)&duw0);
+  if (e == cudaSuccess) e = alloc(sizeof(double), (void**)&demit);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "adjoint buffers");
+  }
+  cudaStream_t stream = s->stream;
+  // forward with checkpoints f^{mK}
+  for (int64_t m = 0; m < M && e == cudaSuccess; ++m) {
+    e = cudaMemcpyAsync(ckpt + (size_t)m * elems, s->f[s->cur], sbytes, cudaMemcpyDeviceToDevice, stream);
+    const int64_t len = std::min<int64_t>(K, nsteps - m * K);
+    for (int64_t t = 0; t < len && e == cudaSuccess; ++t) {
+      e = enqueue_step(s, s->cur, stream);
+      s->cur ^= 1;
+      ++s->steps_done;
+    }
+  }
+  double demit_h = 0.0;
+  if (e == cudaSuccess) e = bgk::launch_adj_lid_table(P, T, dghost, demit, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&demit_h, demit, sizeof(double), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lam0, 0, sbytes, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dlnl, 0, sizeof(double) * ncell, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(duw, 0, sizeof(double) * P.nx, stream);
+  if (e == cudaSuccess)
+    e = bgk::launch_adj_seed(P, T, (const double2*)s->f[s->cur], lam0, dghost, demit_h, Jk, duw0, stream);
+  // backward, segment by segment
+  double2* lam = lam0;
+  double2* lnext = lam1;
+  for (int64_t m = M - 1; m >= 0 && e == cudaSuccess; --m) {
+    const int64_t len = std::min<int64_t>(K, nsteps - m * K);
+    e = cudaMemcpyAsync(seg, ckpt + (size_t)m * elems, sbytes, cudaMemcpyDeviceToDevice, stream);
+    for (int64_t t = 1; t < len && e == cudaSuccess; ++t)
+      e = bgk::launch_step_f64(P, T, seg + (size_t)(t - 1) * elems, seg + (size_t)t * elems, s->mom_tmp, s->err,
+                               stream);
+    for (int64_t t = len - 1; t >= 0 && e == cudaSuccess; --t) {
+      e = bgk::launch_adj_step(P, T, seg + (size_t)t * elems, lam, lamt, lnext, dghost, demit_h, dlnl, duw,
+                               s->err, stream);
+      std::swap(lam, lnext);
+    }
+  }
+  // gather: J, the scalar derivatives (host sums in a fixed order), dJ/df0
+  std::vector<double> h_jk(P.nx), h_duw0(P.nx), h_duw(P.nx), h_dlnl(ncell);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_jk.data(), Jk, sizeof(double) * P.nx, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_duw0.data(), duw0, sizeof(double) * P.nx, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_duw.data(), duw, sizeof(double) * P.nx, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_dlnl.data(), dlnl, sizeof(double) * ncell, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess && dJ_df0)
+    e = cudaMemcpyAsync(dJ_df0, lam, sbytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint");
+  double J = 0.0, duw_t = 0.0, dlnl_t = 0.0;
+  for (int k = 0; k < P.nx; ++k) {
+    J += h_jk[k];
+    duw_t += h_duw0[k] + h_duw[k];
+  }
+  for (int c = 0; c < ncell; ++c) dlnl_t += h_dlnl[c];
+  out[0] = J;
+  out[1] = J + dlnl_t;  // J itself scales with dx
+  out[2] = duw_t;
+  return check_flag(s);
+  BGK_GUARD_END
+}

@@ -87,6 +87,13 @@ cudaError_t launch_build_mixed_tables(const Params& P, const Tables& T, const Mi
                                       cudaStream_t stream);
 size_t step_mixed_smem_bytes(const Params& P, int tile);
 int mixed_groups_per_lane(const Params& P, int tile);
+cudaError_t launch_adj_lid_table(const Params& P, const Tables& T, double2* dghost, double* demit,
+                                 cudaStream_t stream);
+cudaError_t launch_adj_seed(const Params& P, const Tables& T, const double2* f, double2* lam,
+                            const double2* dghost, double demit, double* Jk, double* duw, cudaStream_t stream);
+cudaError_t launch_adj_step(const Params& P, const Tables& T, const double2* fn, const double2* lam_next,
+                            double2* lamt, double2* lam_out, const double2* dghost, double demit,
+                            double* dlnl, double* duw, int* err, cudaStream_t stream);
 cudaError_t launch_msum_moments(const Params& P, int prec, const MixedTables& M, const float2* msum,
                                 double4_32a* mom, cudaStream_t stream);
 cudaError_t prepare_step_mixed(const Params& P, int prec);

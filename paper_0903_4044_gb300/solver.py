@@ -98,11 +98,13 @@ def shock_config(*, mach, nx, length, nvx, vx, omega, cfl, conservative=1, relax
     return cfg, up, down
 
 
-def cavity_config(*, kn, lid_mach, n, nv, vbox, omega, cfl, conservative=1, relax_exact=1,
-                  precision=B.BGK_F64, wall="diffuse", tile_cells=0, stream=None, **_ignored):
-    """cfg for the Sec. 5.1 lid-driven cavity (lid at y = L moving along +x)."""
+def cavity_config(*, kn, lid_mach=None, n, nv, vbox, omega, cfl, conservative=1, relax_exact=1,
+                  precision=B.BGK_F64, wall="diffuse", tile_cells=0, stream=None, lid_speed=None,
+                  **_ignored):
+    """cfg for the Sec. 5.1 lid-driven cavity (lid at y = L moving along +x);
+    ``lid_speed`` (units of sqrt(2 R T0)) overrides the one derived from Mach."""
     side = 1.0 / kn
-    uw = lid_mach * math.sqrt(GAMMA / 2.0)
+    uw = lid_mach * math.sqrt(GAMMA / 2.0) if lid_speed is None else lid_speed
     kind = B.BGK_BC_DIFFUSE if wall == "diffuse" else B.BGK_BC_SPECULAR
     rest = (kind, 1.0, 0.0, 0.0, 1.0)
     lid = (kind, 1.0, uw, 0.0, 1.0)
