@@ -428,6 +428,112 @@ def batch_arm(args, world, rank, local, pg):
     b.close()
 
 
+# algorithmic HBM bytes per point and time step of the gradient evaluation
+# (FP64 state): forward step and its recomputation 32 each; reverse step:
+# collision adjoint reads f^n and lambda^{n+1}, writes lambda~ (48),
+# streaming adjoint reads lambda~, writes lambda^n (32)
+ADJ_BYTES_PER_UPDATE = {"forward": 32.0, "recompute": 32.0, "adj_collide": 48.0, "adj_stream": 32.0}
+
+
+def adjoint_arm(args, world, rank, local, pg):
+    """Gradient of the lid-integrated shear (128^2 cells, 32^2 velocities,
+    Kn 0.1, lid Mach 0.1, 2000 FP64 steps, a checkpoint every 100 steps) with
+    respect to Kn, the lid speed and every entry of f0.  A benchmark step is
+    one whole gradient evaluation: forward with checkpoints, segment
+    recomputation, reverse pass."""
+    import torch
+
+    from paper_0903_4044_gb300 import bgk as B
+    from paper_0903_4044_gb300 import build, solver
+    from paper_0903_4044_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    w = W.CAVITY_128
+    if args.time_steps is not None:
+        w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
+    ncell, nv, _ = sizes(w)
+    nsteps, K = w["steps"], args.checkpoint_every
+    xi = W.perturbation(w.get("seed", 0), ncell, nv)
+    s = solver.make_cavity(w, xi=xi, stream=stream.cuda_stream)
+    f0_host = torch.empty((ncell, nv, 2), dtype=torch.float64, pin_memory=True)
+    B.bgk_get_state(s.h, f0_host.numpy())
+    f0_dev = f0_host.to(f"cuda:{local}")
+    grad_dev = torch.empty_like(f0_dev)
+    grad_host = torch.empty_like(f0_host).pin_memory()
+
+    def one(dev=True):
+        if dev:
+            B.bgk_set_state(s.h, f0_dev)
+            return B.bgk_adjoint_lid_shear(s.h, nsteps, K, grad_dev)
+        B.bgk_set_state(s.h, f0_host.numpy())
+        return B.bgk_adjoint_lid_shear(s.h, nsteps, K, grad_host.numpy())
+
+    for _ in range(args.warmup):
+        out = one()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(pg)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = one()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+    elapsed = max_over_ranks(pg, ev0.elapsed_time(ev1) / 1e3)
+    updates = ncell * nv * nsteps
+    value = world * updates * args.steps / elapsed
+    e2e = None
+    if not args.no_e2e:
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one(dev=False)
+        e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+        e2e = {"value": world * updates * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(f0_host.numel() * 8), "d2h_bytes_per_step": int(grad_host.numel() * 8)}
+    peaks = load_peaks()
+    bytes_eval = sum(ADJ_BYTES_PER_UPDATE.values()) * updates
+    achieved = bytes_eval * args.steps / elapsed / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": args.traffic, "peak_source": peaks["source"],
+            "kernel": "whole gradient evaluation (step_f64 x2, adj_collide, adj_stream)",
+            "bytes_per_update": ADJ_BYTES_PER_UPDATE}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        sample = 3
+        prob, g, h = oracle.cavity_problem(**w, xi=xi)
+        t0 = time.perf_counter()
+        oracle.adjoint_lid_shear(prob, g, h, sample)
+        dt = time.perf_counter() - t0
+        cpu = {"value": ncell * nv * sample / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"oracle forward + reverse pass over {sample} time steps of {w['name']} ({dt:.1f} s; "
+                         "the reverse sweep runs on one core)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"adjoint_{w['name']}", "cells": ncell, "velocities": nv, "time_steps": nsteps,
+                       "checkpoint_every": K, "objective": "lid-integrated shear",
+                       "gradients": "Kn, lid speed, every entry of f0",
+                       "update": "one (cell, velocity) point of one differentiated time step",
+                       "J": out[0], "dJ_dlnL": out[1], "dJ_dUW": out[2],
+                       "l2": "inputs larger than L2 (268 MB state, 27 GB of segment states)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            # forward, recomputation (all but each segment's first state),
+            # two reverse kernels per step, lid table and seed
+            "gpu_launches": args.steps * (4 * nsteps - (nsteps + K - 1) // K + 2),
+        }), flush=True)
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -446,13 +552,14 @@ def main():
                     help="report per-field errors of --precision against the FP64 path instead of timing")
     ap.add_argument("--precision", default="f64", choices=sorted(PRECISION),
                     help="state storage: f64, f32, or bf16 deviation from the absolute Maxwellian")
+    ap.add_argument("--checkpoint-every", type=int, default=100, help="adjoint workload: steps per checkpoint")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
-    w = workload(args.workload) if args.workload != "batch" else None
+    w = workload(args.workload) if args.workload not in ("batch", "adjoint") else None
     if args.time_steps is not None and w is not None:
         w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
-    if args.workload == "batch":
-        batch_arm(args, world, rank, local, pg)
+    if args.workload in ("batch", "adjoint"):
+        (batch_arm if args.workload == "batch" else adjoint_arm)(args, world, rank, local, pg)
         if pg is not None:
             pg.destroy_process_group()
         return

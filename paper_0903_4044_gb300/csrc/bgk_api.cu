@@ -1153,6 +1153,14 @@ bgk_status bgk_batch_autotune(bgk_batch* b, int trial_steps) {
 
 // ---------------------------------------------------------------------------
 // Adjoint driver (kernels in bgk_adjoint.cu).
+//   forward:   f^0 .. f^N, saving f^{mK} (M checkpoints);
+//   seed:      lambda^N = dJ/df^N, J per lid cell, explicit dJ/dU_W;
+//   reverse:   per segment m = M-1 .. 0, recompute f^{mK} .. f^{mK+len}
+//              (with the moments and effective parameters of each step),
+//              then one adj_step launch per step n (streaming adjoint of
+//              step n+1 fused with the collision adjoint of step n; both
+//              read only f^{n+1});
+//   finish:    the streaming adjoint of step 0 gives lambda^0 = dJ/df^0.
 // ---------------------------------------------------------------------------
 extern "C" bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int checkpoint_every, double* dJ_df0,
                                             int on_device, double out[3]) {
@@ -1180,13 +1188,15 @@ extern "C" bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int c
   auto cleanup = [&]() {
     for (void* b : bufs) cudaFree(b);
   };
-  double2 *ckpt = nullptr, *seg = nullptr, *lam0 = nullptr, *lam1 = nullptr, *lamt = nullptr, *dghost = nullptr;
+  double2 *ckpt = nullptr, *seg = nullptr, *lamA = nullptr, *lamB = nullptr, *dghost = nullptr;
+  double4_32a *qbuf = nullptr, *pbuf = nullptr;
   double *dlnl = nullptr, *duw = nullptr, *Jk = nullptr, *duw0 = nullptr, *demit = nullptr;
   cudaError_t e = alloc(sbytes * M, (void**)&ckpt);
-  if (e == cudaSuccess) e = alloc(sbytes * K, (void**)&seg);
-  if (e == cudaSuccess) e = alloc(sbytes, (void**)&lam0);
-  if (e == cudaSuccess) e = alloc(sbytes, (void**)&lam1);
-  if (e == cudaSuccess) e = alloc(sbytes, (void**)&lamt);
+  if (e == cudaSuccess) e = alloc(sbytes * (K + 1), (void**)&seg);
+  if (e == cudaSuccess) e = alloc(sizeof(double4_32a) * ncell * K, (void**)&qbuf);
+  if (e == cudaSuccess) e = alloc(sizeof(double4_32a) * ncell * K, (void**)&pbuf);
+  if (e == cudaSuccess) e = alloc(sbytes, (void**)&lamA);
+  if (e == cudaSuccess) e = alloc(sbytes, (void**)&lamB);
   if (e == cudaSuccess) e = alloc(sizeof(double2) * P.nv, (void**)&dghost);
   if (e == cudaSuccess) e = alloc(sizeof(double) * ncell, (void**)&dlnl);
   if (e == cudaSuccess) e = alloc(sizeof(double) * P.nx, (void**)&duw);
@@ -1195,7 +1205,10 @@ extern "C" bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int c
   if (e == cudaSuccess) e = alloc(sizeof(double), (void**)&demit);
   if (e != cudaSuccess) {
     cleanup();
-    return cuda_fail(e, "adjoint buffers");
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? fail(BGK_ERR_OOM, "adjoint buffers (%lld checkpoints, %d segment states)",
+                                                 (long long)M, K + 1)
+                                          : cuda_fail(e, "adjoint buffers");
   }
   cudaStream_t stream = s->stream;
   // forward with checkpoints f^{mK}
@@ -1212,26 +1225,33 @@ extern "C" bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int c
   if (e == cudaSuccess) e = bgk::launch_adj_lid_table(P, T, dghost, demit, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&demit_h, demit, sizeof(double), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(lam0, 0, sbytes, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lamA, 0, sbytes, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(dlnl, 0, sizeof(double) * ncell, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(duw, 0, sizeof(double) * P.nx, stream);
   if (e == cudaSuccess)
-    e = bgk::launch_adj_seed(P, T, (const double2*)s->f[s->cur], lam0, dghost, demit_h, Jk, duw0, stream);
-  // backward, segment by segment
-  double2* lam = lam0;
-  double2* lnext = lam1;
+    e = bgk::launch_adj_seed(P, T, (const double2*)s->f[s->cur], lamA, dghost, demit_h, Jk, duw0, stream);
+  // reverse, segment by segment
+  double2* lam = lamA;
+  double2* other = lamB;
+  int tilde = 0;
   for (int64_t m = M - 1; m >= 0 && e == cudaSuccess; --m) {
     const int64_t len = std::min<int64_t>(K, nsteps - m * K);
     e = cudaMemcpyAsync(seg, ckpt + (size_t)m * elems, sbytes, cudaMemcpyDeviceToDevice, stream);
-    for (int64_t t = 1; t < len && e == cudaSuccess; ++t)
-      e = bgk::launch_step_f64(P, T, seg + (size_t)(t - 1) * elems, seg + (size_t)t * elems, s->mom_tmp, s->err,
-                               stream);
+    for (int64_t t = 0; t < len && e == cudaSuccess; ++t)
+      e = bgk::launch_step_f64(P, T, seg + (size_t)t * elems, seg + (size_t)(t + 1) * elems, qbuf + (size_t)t * ncell,
+                               s->err, stream, pbuf + (size_t)t * ncell);
     for (int64_t t = len - 1; t >= 0 && e == cudaSuccess; --t) {
-      e = bgk::launch_adj_step(P, T, seg + (size_t)t * elems, lam, lamt, lnext, dghost, demit_h, dlnl, duw,
-                               s->err, stream);
-      std::swap(lam, lnext);
+      e = bgk::launch_adj_step(P, T, seg + (size_t)(t + 1) * elems, qbuf + (size_t)t * ncell,
+                               pbuf + (size_t)t * ncell, lam, tilde, 1, other, dghost, demit_h, dlnl, duw, stream);
+      std::swap(lam, other);
+      tilde = 1;
     }
   }
+  // streaming adjoint of step 0 (seg holds f^0 .. of segment 0)
+  if (e == cudaSuccess)
+    e = bgk::launch_adj_step(P, T, seg, nullptr, nullptr, lam, 1, 0, other, dghost, demit_h, dlnl, duw,
+                             stream);
+  std::swap(lam, other);
   // gather: J, the scalar derivatives (host sums in a fixed order), dJ/df0
   std::vector<double> h_jk(P.nx), h_duw0(P.nx), h_duw(P.nx), h_dlnl(ncell);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_jk.data(), Jk, sizeof(double) * P.nx, cudaMemcpyDeviceToHost, stream);

@@ -68,8 +68,11 @@ struct MixedTables {
 };
 
 // Launchers (bgk_step.cu, bgk_aux.cu, bgk_mixed.cu).  All enqueue on `stream`.
+// One FP64 step fin -> fout; mom[cell] receives the moments (n, ux, uy,
+// theta) of the post-streaming state, par[cell] (when not null) the
+// effective Maxwellian parameters the relaxation used.
 cudaError_t launch_step_f64(const Params& P, const Tables& T, const double2* fin, double2* fout,
-                            double4_32a* mom, int* err, cudaStream_t stream);
+                            double4_32a* mom, int* err, cudaStream_t stream, double4_32a* par = nullptr);
 cudaError_t launch_build_tables(const Params& P, double* cx, double* cy, double4_32a* coef, int* shift,
                                 double2* cxy, int* vinfo, double2* ghost, double* emitted,
                                 cudaStream_t stream);
@@ -87,13 +90,15 @@ cudaError_t launch_build_mixed_tables(const Params& P, const Tables& T, const Mi
                                       cudaStream_t stream);
 size_t step_mixed_smem_bytes(const Params& P, int tile);
 int mixed_groups_per_lane(const Params& P, int tile);
+// Reverse pass of the lid shear (bgk_adjoint.cu).
 cudaError_t launch_adj_lid_table(const Params& P, const Tables& T, double2* dghost, double* demit,
                                  cudaStream_t stream);
 cudaError_t launch_adj_seed(const Params& P, const Tables& T, const double2* f, double2* lam,
                             const double2* dghost, double demit, double* Jk, double* duw, cudaStream_t stream);
-cudaError_t launch_adj_step(const Params& P, const Tables& T, const double2* fn, const double2* lam_next,
-                            double2* lamt, double2* lam_out, const double2* dghost, double demit,
-                            double* dlnl, double* duw, int* err, cudaStream_t stream);
+cudaError_t launch_adj_step(const Params& P, const Tables& T, const double2* fn1,
+                            const double4_32a* qn, const double4_32a* pn, const double2* lam_in, int tilde,
+                            int collide, double2* out, const double2* dghost, double demit, double* dlnl,
+                            double* duw, cudaStream_t stream);
 cudaError_t launch_msum_moments(const Params& P, int prec, const MixedTables& M, const float2* msum,
                                 double4_32a* mom, cudaStream_t stream);
 cudaError_t prepare_step_mixed(const Params& P, int prec);

@@ -204,7 +204,8 @@ __device__ __forceinline__ void axis_sums(const double* __restrict__ c, int n, d
 template <int DIM, int G>
 __device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, const double (*sums)[4],
                                  double* __restrict__ phx, double* __restrict__ phy, double* sb,
-                                 double* sk, int* sok, double4_32a* __restrict__ mom, int* __restrict__ err) {
+                                 double* sk, int* sok, double4_32a* __restrict__ mom,
+                                 double4_32a* __restrict__ par, int* __restrict__ err) {
   constexpr int L = 32 / G;
   const int lane = threadIdx.x & 31, c = lane / L, sub = lane % L;
   const int cell = cell0 + c;
@@ -263,6 +264,7 @@ __device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, co
     sok[c] = ok ? 1 : 0;
     if (live) {
       mom[cell] = make_double4_32a(qm[0], qm[1], qm[2], qm[3]);
+      if (par) par[cell] = make_double4_32a(p[0], p[1], p[2], p[3]);
       if (!ok) atomicOr(err, E.fail ? ERR_EFFECTIVE : ERR_MOMENT);
     }
   }
@@ -273,7 +275,8 @@ __device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, co
 template <int DIM, int G>
 __global__ void __launch_bounds__(32 * G)
     step_f64_kernel(const double2* __restrict__ fin, double2* __restrict__ fout,
-                    double4_32a* __restrict__ mom, const Params P, const Tables T, int* __restrict__ err) {
+                    double4_32a* __restrict__ mom, double4_32a* __restrict__ par, const Params P,
+                    const Tables T, int* __restrict__ err) {
   extern __shared__ double4_32a smem4[];
   double2* ftile = reinterpret_cast<double2*>(smem4);
   double* phx = reinterpret_cast<double*>(ftile + (size_t)G * P.nv);
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(32 * G)
 
   if (live) stream_cell<DIM>(P, T, fin, cell, tile, s_sum[warp]);
   __syncthreads();
-  if (warp == 0) maxwellian_cells<DIM, G>(P, T, blockIdx.x * G, s_sum, phx, phy, s_b, s_k, s_ok, mom, err);
+  if (warp == 0) maxwellian_cells<DIM, G>(P, T, blockIdx.x * G, s_sum, phx, phy, s_b, s_k, s_ok, mom, par, err);
   __syncthreads();
   if (!live) return;
 
@@ -326,10 +329,10 @@ size_t step_smem(const Params& P, int G) {
 
 template <int DIM, int G>
 cudaError_t launch_g(const Params& P, const Tables& T, const double2* fin, double2* fout,
-                     double4_32a* mom, int* err, cudaStream_t stream) {
+                     double4_32a* mom, double4_32a* par, int* err, cudaStream_t stream) {
   const int ncell = P.nx * P.ny;
   const unsigned grid = (unsigned)((ncell + G - 1) / G);
-  step_f64_kernel<DIM, G><<<grid, 32 * G, step_smem(P, G), stream>>>(fin, fout, mom, P, T, err);
+  step_f64_kernel<DIM, G><<<grid, 32 * G, step_smem(P, G), stream>>>(fin, fout, mom, par, P, T, err);
   return cudaGetLastError();
 }
 
@@ -344,12 +347,12 @@ cudaError_t prepare_g(const Params&) {
 
 template <int DIM>
 cudaError_t dispatch(const Params& P, const Tables& T, const double2* fin, double2* fout,
-                     double4_32a* mom, int* err, cudaStream_t stream) {
+                     double4_32a* mom, double4_32a* par, int* err, cudaStream_t stream) {
   switch (P.tile) {
-    case 1: return launch_g<DIM, 1>(P, T, fin, fout, mom, err, stream);
-    case 2: return launch_g<DIM, 2>(P, T, fin, fout, mom, err, stream);
-    case 4: return launch_g<DIM, 4>(P, T, fin, fout, mom, err, stream);
-    case 8: return launch_g<DIM, 8>(P, T, fin, fout, mom, err, stream);
+    case 1: return launch_g<DIM, 1>(P, T, fin, fout, mom, par, err, stream);
+    case 2: return launch_g<DIM, 2>(P, T, fin, fout, mom, par, err, stream);
+    case 4: return launch_g<DIM, 4>(P, T, fin, fout, mom, par, err, stream);
+    case 8: return launch_g<DIM, 8>(P, T, fin, fout, mom, par, err, stream);
   }
   return cudaErrorInvalidValue;
 }
@@ -374,9 +377,9 @@ cudaError_t prepare_step_f64(const Params& P) {
 }
 
 cudaError_t launch_step_f64(const Params& P, const Tables& T, const double2* fin, double2* fout,
-                            double4_32a* mom, int* err, cudaStream_t stream) {
-  return P.dim == 1 ? dispatch<1>(P, T, fin, fout, mom, err, stream)
-                    : dispatch<2>(P, T, fin, fout, mom, err, stream);
+                            double4_32a* mom, int* err, cudaStream_t stream, double4_32a* par) {
+  return P.dim == 1 ? dispatch<1>(P, T, fin, fout, mom, par, err, stream)
+                    : dispatch<2>(P, T, fin, fout, mom, par, err, stream);
 }
 
 }  // namespace bgk
