@@ -428,11 +428,13 @@ def batch_arm(args, world, rank, local, pg):
     b.close()
 
 
-# algorithmic HBM bytes per point and time step of the gradient evaluation
-# (FP64 state): forward step and its recomputation 32 each; reverse step:
-# collision adjoint reads f^n and lambda^{n+1}, writes lambda~ (48),
-# streaming adjoint reads lambda~, writes lambda^n (32)
-ADJ_BYTES_PER_UPDATE = {"forward": 32.0, "recompute": 32.0, "adj_collide": 48.0, "adj_stream": 32.0}
+# Algorithmic cost per point and time step of the gradient evaluation (FP64
+# state, FMA = 2 flops).  Forward step and its recomputation: 32 B and 24
+# flops each.  Reverse step (adj_step_kernel): reads lambda~^{n+1} and
+# f^{n+1}, writes lambda~^n (48 B); gather 10 flops, collision sums 17,
+# output polynomial 10 (37 flops).
+ADJ_BYTES_PER_UPDATE = {"forward": 32.0, "recompute": 32.0, "adj_step": 48.0}
+ADJ_FLOPS_PER_UPDATE = {"forward": 24.0, "recompute": 24.0, "adj_step": 37.0}
 
 
 def adjoint_arm(args, world, rank, local, pg):
@@ -497,11 +499,15 @@ def adjoint_arm(args, world, rank, local, pg):
                "h2d_bytes_per_step": int(f0_host.numel() * 8), "d2h_bytes_per_step": int(grad_host.numel() * 8)}
     peaks = load_peaks()
     bytes_eval = sum(ADJ_BYTES_PER_UPDATE.values()) * updates
-    achieved = bytes_eval * args.steps / elapsed / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": args.traffic, "peak_source": peaks["source"],
-            "kernel": "whole gradient evaluation (step_f64 x2, adj_collide, adj_stream)",
-            "bytes_per_update": ADJ_BYTES_PER_UPDATE}
+    flops_eval = sum(ADJ_FLOPS_PER_UPDATE.values()) * updates
+    hbm = bytes_eval * args.steps / elapsed / 1e9
+    alu = flops_eval * args.steps / elapsed / 1e12
+    roof = {"bound": "alu", "achieved": alu, "peak": FP64_NOMINAL_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": alu / (FP64_NOMINAL_FLOPS / 1e12), "traffic": args.traffic,
+            "peak_source": "nominal FP64 (unit counts x clock)",
+            "kernel": "whole gradient evaluation (step_f64_kernel x2, adj_step_kernel)",
+            "flops_per_update": ADJ_FLOPS_PER_UPDATE, "bytes_per_update": ADJ_BYTES_PER_UPDATE,
+            "hbm_gbs": hbm, "hbm_frac": hbm / peaks["hbm_gbs"], "hbm_peak_source": peaks["source"]}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -527,9 +533,9 @@ def adjoint_arm(args, world, rank, local, pg):
                        "J": out[0], "dJ_dlnL": out[1], "dJ_dUW": out[2],
                        "l2": "inputs larger than L2 (268 MB state, 27 GB of segment states)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            # forward, recomputation (all but each segment's first state),
-            # two reverse kernels per step, lid table and seed
-            "gpu_launches": args.steps * (4 * nsteps - (nsteps + K - 1) // K + 2),
+            # forward, recomputation, one reverse kernel per step plus the
+            # final streaming adjoint, lid table and seed
+            "gpu_launches": args.steps * (3 * nsteps + 3),
         }), flush=True)
     s.close()
 
