@@ -135,7 +135,7 @@ double max_abs_centre(double vmin, double vmax, int n) {
 }
 
 size_t step_smem(const bgk::Params& P, int prec, int tile) {
-  return prec == BGK_F64 ? bgk::step_f64_smem_bytes(P, tile) : bgk::step_mixed_smem_bytes(P, tile);
+  return prec == BGK_F64 ? bgk::step_f64_smem_bytes(P, tile) : bgk::step_mixed_smem_bytes(P, tile, prec == BGK_BF16_DEV ? bgk::PREC_BF16 : bgk::PREC_F32);
 }
 
 // All configuration checks, before any CUDA call.  Fills P and max_courant.
@@ -284,9 +284,8 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
 int auto_tile(const bgk::Params& P, int prec, int sms) {
   const long long ncell = (long long)P.nx * P.ny;
   for (int t : {8, 4, 2}) {
-    // reduced precisions: at most 16 velocities per lane (more spills registers)
-    if (prec != BGK_F64 && (bgk::mixed_groups_per_lane(P, t) == 0 || bgk::mixed_groups_per_lane(P, t) > 4))
-      continue;
+    // reduced precisions: at most 24 velocities per lane (instantiated)
+    if (prec != BGK_F64 && bgk::mixed_groups_per_lane(P, t) == 0) continue;
     if (step_smem(P, prec, t) <= kAutoSmem && (ncell + t - 1) / t >= 2LL * sms) return t;
   }
   return 1;

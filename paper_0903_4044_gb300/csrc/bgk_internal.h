@@ -88,7 +88,7 @@ cudaError_t launch_wall_fluxes(const Params& P, const Tables& T, const double2* 
                                double4_32a* out, cudaStream_t stream);
 cudaError_t launch_build_mixed_tables(const Params& P, const Tables& T, const MixedTables& M,
                                       cudaStream_t stream);
-size_t step_mixed_smem_bytes(const Params& P, int tile);
+size_t step_mixed_smem_bytes(const Params& P, int tile, int prec);
 int mixed_groups_per_lane(const Params& P, int tile);
 // Reverse pass of the lid shear (bgk_adjoint.cu).
 cudaError_t launch_adj_lid_table(const Params& P, const Tables& T, double2* dghost, double* demit,

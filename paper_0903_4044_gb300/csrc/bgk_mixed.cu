@@ -167,6 +167,11 @@ __device__ __forceinline__ float2 ghost_m(const Params& P, const MixedTables& M,
 // from streaming (phase 1) to relaxation (phase 3).  Phase 2 runs on the
 // cell's first warp, on the FP32 pipe except the normalisation.
 
+// Bytes of the Gaussian factors of G cells in shared memory.
+__host__ __device__ __forceinline__ size_t mixed_factor_bytes(const Params& P, int G) {
+  return (sizeof(float) * (size_t)G * (P.nvx + P.nvy) + 15) & ~(size_t)15;
+}
+
 // Where a cell sits: which faces it touches, and n_W of its diffuse faces.
 struct CellCtx {
   size_t c0, row;
@@ -284,129 +289,165 @@ __device__ __forceinline__ float warp_sum_f(float x) {
   return x;
 }
 
-// Phase 2 for one cell, one warp: moments from the float-float sums, nu and
-// the relaxation weight, FP32 Gaussians at (U, theta), two linearised
-// effective-parameter updates (A3, FP32: the reduced forms only need the
-// correction to FP32 resolution), FP64 normalisation, factors to shared
-// memory.  Also publishes the float-float sums (msum) from which bgk_moments
-// forms FP64 moments on request.
-template <int PREC>
-__device__ void cell_params_f32(const Params& P, const MixedTables& M, int cell, const float2 (*part)[4],
-                                int wpc, float* __restrict__ px, float* __restrict__ py, float* sa, float* sk,
-                                int* sok, float2* __restrict__ msum, int* __restrict__ err) {
+// Phase 2, the per-cell parameters, spread over the cell's WPC warps in
+// three parts separated by CTA barriers (every warp of the CTA calls each
+// part; cells outside the grid only take part in the barriers):
+//   2a  every warp: the cell's moments from the float-float velocity sums
+//       (lane-parallel tree over the warps' partials), nu and the relaxation
+//       weight; then one FP32 Gaussian exp(-(c - u)^2 / theta) per lane for
+//       the x and y factors, stored to shared memory, and the lane's share
+//       of the central sums sum d^m e (m = 0..4) reduced over the warp;
+//   2b  the cell's first warp: two linearised effective-parameter updates
+//       (A3, FP32: the reduced forms only need the correction to FP32
+//       resolution) and the normalisation n / (pi theta), evaluated in
+//       float-float (at least 44 significant bits) and rounded once;
+//   2c  every warp: the Gaussian factors moved from (u, theta) to the
+//       effective parameters and scaled by a n/(pi theta).
+// The first warp also publishes the float-float sums (msum) from which
+// bgk_moments forms FP64 moments on request.
+
+// Per-cell scalars shared between the parts.
+struct CellPar {
+  float n, ux, uy, th, a;  // moments of f~ and the relaxation weight
+  float ap, w1x, w1y, w2;  // factor update: ap e (1 + d (w1 + d w2))
+  float kappa;             // H = kappa G
+  int ok;
+};
+
+// a * p0 / (pi * p3) with float-float intermediates, rounded once to FP32.
+__device__ __forceinline__ float ff_norm(float a, float p0, float p3) {
+  const float pi_h = 3.14159274101257324f;  // pi rounded to FP32
+  const float pi_l = -8.74227766e-08f;      // pi - pi_h
+  const float dh = pi_h * p3;
+  const float dl = fmaf(pi_h, p3, -dh) + pi_l * p3;  // pi p3 = dh + dl
+  const float nh = a * p0;
+  const float nl = fmaf(a, p0, -nh);  // a p0 = nh + nl exactly
+  const float rd = __frcp_rn(dh);
+  const float q1 = nh * rd;
+  float r = fmaf(-q1, dh, nh);  // exact residual of q1 dh
+  r = fmaf(-q1, dl, r) + nl;
+  return fmaf(r, rd, q1);
+}
+
+template <int PREC, int WPC>
+__device__ __forceinline__ void cell_moments(const Params& P, const MixedTables& M, int cell, int wc,
+                                             const float2 (*part)[4], CellPar& cp, float2* __restrict__ msum) {
   const int lane = threadIdx.x & 31;
-  float h[4], l[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    h[k] = part[0][k].x;
-    l[k] = part[0][k].y;
-    for (int w = 1; w < wpc; ++w) ff_add(h[k], l[k], part[w][k].x, part[w][k].y);
+  // lane = 4 w + k holds partial w of value k; tree over w
+  const int k = lane & 3, w = lane >> 2;
+  float h = 0.f, l = 0.f;
+  if (w < WPC) {
+    const float2 v = part[w][k];
+    h = v.x;
+    l = v.y;
   }
-  if (lane < 4) {
-    const int k = lane;
-    msum[(size_t)cell * 4 + k] = make_float2(k == 0 ? h[0] : k == 1 ? h[1] : k == 2 ? h[2] : h[3],
-                                             k == 0 ? l[0] : k == 1 ? l[1] : k == 2 ? l[2] : l[3]);
-  }
-  float S[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (Store<PREC>::delta) ff_add(h[k], l[k], M.mabs_ff[k].x, M.mabs_ff[k].y);
-    S[k] = h[k] + l[k];
-  }
-  const float dv = (float)P.dv;
-  float n = S[0] * dv, ux = S[1] / S[0], uy = S[2] / S[0];
-  float th = (2.0f / 3.0f) * (S[3] / S[0] - (ux * ux + uy * uy));
-  bool ok = n > 0.f && th > 0.f && isfinite(n) && isfinite(ux) && isfinite(uy) && isfinite(th);
+  if (WPC > 1) ff_xor(h, l, 4);
+  if (WPC > 2) ff_xor(h, l, 8);
+  if (WPC > 4) ff_xor(h, l, 16);
+  if (wc == 0 && lane < 4) msum[(size_t)cell * 4 + lane] = make_float2(h, l);
+  if (Store<PREC>::delta) ff_add(h, l, M.mabs_ff[k].x, M.mabs_ff[k].y);
+  const float sk = h + l;
+  const float S0 = __shfl_sync(0xffffffffu, sk, 0), S1 = __shfl_sync(0xffffffffu, sk, 1);
+  const float S2 = __shfl_sync(0xffffffffu, sk, 2), S3 = __shfl_sync(0xffffffffu, sk, 3);
+  const float r0 = __frcp_rn(S0);
+  float n = S0 * (float)P.dv, ux = S1 * r0, uy = S2 * r0;
+  float th = (2.0f / 3.0f) * (S3 * r0 - (ux * ux + uy * uy));
+  const bool ok = n > 0.f && th > 0.f && isfinite(n) && isfinite(ux) && isfinite(uy) && isfinite(th);
   if (!ok) {
     n = 1.f;
     ux = uy = 0.f;
     th = 1.f;
   }
   const float nu = n * (P.omega == 0.5 ? sqrtf(th) : powf(th, (float)(1.0 - P.omega)));
-  const float a = P.relax_exact ? 1.0f - expf(-nu * (float)P.dt) : nu * (float)P.dt;
-  // Gaussians at q, and their central sums M_m = sum d^m e
-  const float inv = 1.0f / th;
-  float Mx[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, My[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int j = lane; j < P.nvx; j += 32) {
-    const float d = M.cx[j] - ux;
+  cp.n = n;
+  cp.ux = ux;
+  cp.uy = uy;
+  cp.th = th;
+  cp.a = P.relax_exact ? 1.0f - expf(-nu * (float)P.dt) : nu * (float)P.dt;
+  cp.ok = ok;
+}
+
+// 2a: Gaussian factors at (u, theta) for j = wc*32 + lane, ... (x: j < nvx,
+// y: the rest) into px (y factors follow in py); returns the lane's central
+// sums (x in Mx, y in My).
+template <int WPC>
+__device__ __forceinline__ void cell_gauss(const Params& P, const MixedTables& M, int wc, const CellPar& cp,
+                                           float* __restrict__ px, float* __restrict__ py, float (&Mx)[5],
+                                           float (&My)[5]) {
+  const int lane = threadIdx.x & 31;
+  const float inv = __frcp_rn(cp.th);
+  for (int m = 0; m < 5; ++m) Mx[m] = My[m] = 0.f;
+  for (int j = wc * 32 + lane; j < P.nvx + P.nvy; j += WPC * 32) {
+    const bool isx = j < P.nvx;
+    const float d = isx ? M.cx[j] - cp.ux : M.cy[j - P.nvx] - cp.uy;
     const float e = expf(-(d * d) * inv);
-    px[j] = e;
-    float t = e;
-    Mx[0] += t;
-    t *= d;
-    Mx[1] += t;
-    t *= d;
-    Mx[2] += t;
-    t *= d;
-    Mx[3] += t;
-    t *= d;
-    Mx[4] += t;
-  }
-  for (int j = lane; j < P.nvy; j += 32) {
-    const float d = M.cy[j] - uy;
-    const float e = expf(-(d * d) * inv);
-    py[j] = e;
-    float t = e;
-    My[0] += t;
-    t *= d;
-    My[1] += t;
-    t *= d;
-    My[2] += t;
-    t *= d;
-    My[3] += t;
-    t *= d;
-    My[4] += t;
-  }
-  float p[4] = {n, ux, uy, th};
-  if (P.conservative) {
+    if (isx) px[j] = e;
+    else py[j - P.nvx] = e;
+    float t[5];
+    t[0] = e;
+#pragma unroll
+    for (int m = 1; m < 5; ++m) t[m] = t[m - 1] * d;
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-      Mx[m] = warp_sum_f(Mx[m]);
-      My[m] = warp_sum_f(My[m]);
+      Mx[m] += isx ? t[m] : 0.f;
+      My[m] += isx ? 0.f : t[m];
     }
-    const float q[4] = {n, ux, uy, th};
+  }
+}
+
+// 2b (first warp of the cell): effective parameters and normalisation.
+__device__ __forceinline__ void cell_effective(const Params& P, CellPar& cp, const float (&Mx)[5],
+                                               const float (&My)[5]) {
+  const float dv = (float)P.dv;
+  const float inv = __frcp_rn(cp.th);
+  const float q[4] = {cp.n, cp.ux, cp.uy, cp.th};
+  float p[4] = {cp.n, cp.ux, cp.uy, cp.th};
+  bool ok = cp.ok != 0;
+  if (P.conservative) {
     for (int it = 0; it < 2; ++it) {
-      const float w2 = (p[3] - th) * inv * inv;
-      const float w1x = 2.f * (p[1] - ux) * inv, w1y = 2.f * (p[2] - uy) * inv;
+      const float w2 = (p[3] - cp.th) * inv * inv;
+      const float w1x = 2.f * (p[1] - cp.ux) * inv, w1y = 2.f * (p[2] - cp.uy) * inv;
       float Sx[3], Sy[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         Sx[m] = Mx[m] + w1x * Mx[m + 1] + w2 * Mx[m + 2];
         Sy[m] = My[m] + w1y * My[m + 1] + w2 * My[m + 2];
       }
-      const float mux = Sx[1] / Sx[0], muy = Sy[1] / Sy[0];
+      const float rx = __frcp_rn(Sx[0]), ry = __frcp_rn(Sy[0]);
+      const float mux = Sx[1] * rx, muy = Sy[1] * ry;
       float d[4];
-      d[0] = p[0] / (3.14159265f * p[3]) * dv * Sx[0] * Sy[0];
-      d[1] = ux + mux;
-      d[2] = uy + muy;
-      d[3] = (2.f / 3.f) * ((Sx[2] / Sx[0] - mux * mux) + (Sy[2] / Sy[0] - muy * muy) + 0.5f * p[3]);
+      d[0] = p[0] * __frcp_rn(3.14159265f * p[3]) * dv * Sx[0] * Sy[0];
+      d[1] = cp.ux + mux;
+      d[2] = cp.uy + muy;
+      d[3] = (2.f / 3.f) * ((Sx[2] * rx - mux * mux) + (Sy[2] * ry - muy * muy) + 0.5f * p[3]);
 #pragma unroll
       for (int k = 0; k < 4; ++k) p[k] += q[k] - d[k];
     }
     if (!(p[0] > 0.f) || !(p[3] > 0.f) || !isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2]) ||
-        !isfinite(p[3])) {
+        !isfinite(p[3]))
       ok = false;
-    }
   }
-  if (ok) {
-    // the Maxwellian normalisation n / (pi theta) in FP64
-    const float ap = (float)((double)a * ((double)p[0] / (kPi() * (double)p[3])));
-    const float w2 = (p[3] - th) * inv * inv;
-    const float w1x = 2.f * (p[1] - ux) * inv, w1y = 2.f * (p[2] - uy) * inv;
-    for (int j = lane; j < P.nvx; j += 32) {
-      const float d = M.cx[j] - ux;
-      px[j] = ap * (px[j] * fmaf(d, fmaf(d, w2, w1x), 1.0f));
+  cp.ok = ok;
+  cp.ap = ok ? ff_norm(cp.a, p[0], p[3]) : 0.f;
+  cp.w2 = (p[3] - cp.th) * inv * inv;
+  cp.w1x = 2.f * (p[1] - cp.ux) * inv;
+  cp.w1y = 2.f * (p[2] - cp.uy) * inv;
+  cp.kappa = 0.5f * p[3];
+}
+
+// 2c: move the factors to the effective parameters and scale by ap.
+template <int WPC>
+__device__ __forceinline__ void cell_factors(const Params& P, const MixedTables& M, int wc, const CellPar& cp,
+                                             float* __restrict__ px, float* __restrict__ py) {
+  const int lane = threadIdx.x & 31;
+  for (int j = wc * 32 + lane; j < P.nvx + P.nvy; j += WPC * 32) {
+    if (j < P.nvx) {
+      const float d = M.cx[j] - cp.ux;
+      px[j] = cp.ap * (px[j] * fmaf(d, fmaf(d, cp.w2, cp.w1x), 1.0f));
+    } else {
+      const float d = M.cy[j - P.nvx] - cp.uy;
+      py[j - P.nvx] = py[j - P.nvx] * fmaf(d, fmaf(d, cp.w2, cp.w1y), 1.0f);
     }
-    for (int j = lane; j < P.nvy; j += 32) {
-      const float d = M.cy[j] - uy;
-      py[j] = py[j] * fmaf(d, fmaf(d, w2, w1y), 1.0f);
-    }
-  }
-  if (lane == 0) {
-    *sa = a;
-    *sk = 0.5f * p[3];
-    *sok = ok ? 1 : 0;
-    if (!ok) atomicOr(err, ERR_MOMENT);
   }
 }
 
@@ -442,9 +483,11 @@ __device__ __forceinline__ void store_result(void* fout, size_t idx, const float
 
 }  // namespace
 
-// 768 resident threads per SM at most 80 registers each.
+// 768 resident threads per SM at most 80 registers each; FP32 with 6 groups
+// per lane gets 128 registers and 2 CTAs per SM instead (measured faster than
+// spilling; BF16 keeps 3 CTAs and spills a little, also measured).
 template <int PREC, int G, int MGL>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, (PREC == PREC_F32 && MGL >= 6) ? 2 : 3)
     step_mixed_kernel(const void* __restrict__ fin, void* __restrict__ fout, float2* __restrict__ msum,
                       const Params P, const MixedTables M, int* __restrict__ err) {
   constexpr int WPC = 8 / G;
@@ -452,8 +495,8 @@ __global__ void __launch_bounds__(256, 3)
   float* phx = reinterpret_cast<float*>(smemf4);
   float* phy = phx + G * P.nvx;
   __shared__ float2 s_part[G][WPC][4];
-  __shared__ float s_a[G], s_k[G];
-  __shared__ int s_ok[G];
+  __shared__ float s_gp[G][WPC][10];
+  __shared__ CellPar s_cp[G];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = warp / WPC, wc = warp % WPC;
@@ -498,17 +541,53 @@ __global__ void __launch_bounds__(256, 3)
     if ((lane & 7) == 0) s_part[c][wc][lane >> 3] = make_float2(oh, ol);
   }
   __syncthreads();
-  if (live && wc == 0)
-    cell_params_f32<PREC>(P, M, cell, s_part[c], WPC, phx + c * P.nvx, phy + c * P.nvy, &s_a[c], &s_k[c],
-                          &s_ok[c], msum, err);
+  // phase 2 (see cell_moments .. cell_factors)
+  float* pxc = phx + c * P.nvx;
+  float* pyc = phy + c * P.nvy;
+  CellPar cp;
+  if (live) {
+    cell_moments<PREC, WPC>(P, M, cell, wc, s_part[c], cp, msum);
+    float Mx[5], My[5];
+    cell_gauss<WPC>(P, M, wc, cp, pxc, pyc, Mx, My);
+    // warp totals of the 10 central sums: lane 4 m + (0: x, 1: y) picks them up
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      Mx[m] = warp_sum_f(Mx[m]);
+      My[m] = warp_sum_f(My[m]);
+    }
+    if (lane < 10) s_gp[c][wc][lane] = lane < 5 ? Mx[lane] : My[lane - 5];
+  }
+  __syncthreads();
+  if (live && wc == 0) {
+    float Mx[5], My[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      Mx[m] = s_gp[c][0][m];
+      My[m] = s_gp[c][0][5 + m];
+      for (int w = 1; w < WPC; ++w) {
+        Mx[m] += s_gp[c][w][m];
+        My[m] += s_gp[c][w][5 + m];
+      }
+    }
+    cell_effective(P, cp, Mx, My);
+    if (lane == 0) {
+      s_cp[c] = cp;
+      if (!cp.ok) atomicOr(err, ERR_MOMENT);
+    }
+  }
+  __syncthreads();
+  if (live) {
+    cp = s_cp[c];
+    if (cp.ok) cell_factors<WPC>(P, M, wc, cp, pxc, pyc);
+  }
   __syncthreads();
   if (!live) return;
 
   // A4: f^{n+1} = f~ + (a Phi - a f~)
-  const float a = s_a[c], kappa = s_k[c];
-  const bool ok = s_ok[c] != 0;
-  const float* px = phx + c * P.nvx;
-  const float* py = phy + c * P.nvy;
+  const float a = cp.a, kappa = cp.kappa;
+  const bool ok = cp.ok != 0;
+  const float* px = pxc;
+  const float* py = pyc;
 #pragma unroll
   for (int k = 0; k < MGL; ++k) {
     const int g = lic + k * 32 * WPC;
@@ -675,14 +754,16 @@ cudaError_t launch_from_f64(const Params& P, int prec, const MixedTables& M, con
 // ---- launch ------------------------------------------------------------------
 namespace {
 
-size_t mixed_smem(const Params& P, int G) { return sizeof(float) * (size_t)G * (P.nvx + P.nvy); }
+// The Gaussian factors of G cells.
+size_t mixed_smem(const Params& P, int G, int) { return mixed_factor_bytes(P, G); }
 
 template <int PREC, int G, int MGL>
 cudaError_t launch_mg(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
                       int* err, cudaStream_t stream) {
   const int ncell = P.nx * P.ny;
   const unsigned grid = (unsigned)((ncell + G - 1) / G);
-  step_mixed_kernel<PREC, G, MGL><<<grid, 256, mixed_smem(P, G), stream>>>(fin, fout, msum, P, M, err);
+  const size_t smem = mixed_smem(P, G, PREC);
+  step_mixed_kernel<PREC, G, MGL><<<grid, 256, smem, stream>>>(fin, fout, msum, P, M, err);
   return cudaGetLastError();
 }
 
@@ -711,7 +792,7 @@ cudaError_t dispatch_m(const Params& P, const MixedTables& M, const void* fin, v
 
 }  // namespace
 
-size_t step_mixed_smem_bytes(const Params& P, int tile) { return mixed_smem(P, tile); }
+size_t step_mixed_smem_bytes(const Params& P, int tile, int prec) { return mixed_smem(P, tile, prec); }
 
 // Groups of 4 velocities per lane when a cell has 256/tile lanes, rounded up
 // to an instantiated count (2, 4 or 6); 0 if more than 6 would be needed.
