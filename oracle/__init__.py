@@ -27,6 +27,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bgk_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "bgk_oracle3v.c")]
+_HDRS = [os.path.join(_HERE, "bgk_oracle.h"), os.path.join(_HERE, "bgk_oracle3v.h")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 BC_INFLOW, BC_DIFFUSE, BC_SPECULAR = 0, 1, 2
@@ -35,15 +37,15 @@ GAMMA = 5.0 / 3.0  # monatomic gas (Sec. 4.1)
 
 
 def build(force: bool = False) -> str:
-    """Compile ``bgk_oracle.c`` into ``liboracle.so`` (gcc, OpenMP, no FMA contraction)."""
+    """Compile the oracle's C sources into ``liboracle.so`` (gcc, OpenMP, no FMA contraction)."""
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "bgk_oracle.h"))
+        os.path.getmtime(f) for f in _SRCS + _HDRS
     ):
         return _LIB_PATH
     cmd = [
         "gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
         "-ffp-contract=off", "-fno-fast-math", "-Wall",
-        _SRC, "-o", _LIB_PATH + ".tmp", "-lm",
+        *_SRCS, "-o", _LIB_PATH + ".tmp", "-lm",
     ]
     subprocess.run(cmd, check=True)
     os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
@@ -61,6 +63,17 @@ class OrcConfig(ctypes.Structure):
         ("omega", ctypes.c_double), ("dt", ctypes.c_double),
         ("conservative", ctypes.c_int), ("relax_exact", ctypes.c_int),
         ("bc_kind", ctypes.c_int * 4), ("bc_state", (ctypes.c_double * 4) * 4),
+    ]
+
+
+class Orc3Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("x0", ctypes.c_double), ("lx", ctypes.c_double),
+        ("nvx", ctypes.c_int), ("nvy", ctypes.c_int), ("nvz", ctypes.c_int),
+        ("vmin", ctypes.c_double * 3), ("vmax", ctypes.c_double * 3),
+        ("omega", ctypes.c_double), ("dt", ctypes.c_double),
+        ("conservative", ctypes.c_int), ("relax_exact", ctypes.c_int),
+        ("inflow", (ctypes.c_double * 5) * 2),
     ]
 
 
@@ -98,6 +111,21 @@ def lib():
         L.orc_lid_shear.argtypes = [_C, _D, _D]
         L.orc_lid_shear.restype = ctypes.c_double
         L.orc_adjoint_lid_shear.argtypes = [_C, _D, _D, ctypes.c_long, _D, _D, _D]
+        C3 = ctypes.POINTER(Orc3Config)
+        L.orc3_nv.argtypes = [C3]
+        L.orc3_c.argtypes = [C3, ctypes.c_int, ctypes.c_int]
+        L.orc3_c.restype = ctypes.c_double
+        L.orc3_dv.argtypes = [C3]
+        L.orc3_dv.restype = ctypes.c_double
+        L.orc3_dt_from_cfl.argtypes = [C3, ctypes.c_double]
+        L.orc3_dt_from_cfl.restype = ctypes.c_double
+        L.orc3_maxwellian.argtypes = [C3, _D, _D]
+        L.orc3_moments.argtypes = [C3, _D, _D]
+        L.orc3_effective_params.argtypes = [C3, _D, _D]
+        L.orc3_init_step.argtypes = [C3, ctypes.c_double, _D, _D, _D]
+        L.orc3_stream.argtypes = [C3, _D, _D]
+        L.orc3_relax.argtypes = [C3, _D, _D]
+        L.orc3_step.argtypes = [C3, _D, ctypes.c_long, _D]
         _lib = L
     return _lib
 
@@ -310,3 +338,112 @@ def cavity_problem(*, kn, lid_mach, n, nv, vbox, omega, cfl, steps, xi=None, amp
     prob = Problem(cfg, steps, {"uw": uw, "side": side})
     g, h = init_uniform(prob, rest, xi, amp)
     return prob, g, h
+
+
+
+# --- full 3D velocity grid, one spatial dimension (bgk_oracle3v.c) -------
+@dataclass
+class Problem3v:
+    """A configured full-velocity-grid problem: the oracle's config and derived values."""
+
+    cfg: Orc3Config
+    steps: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nv(self) -> int:
+        return lib().orc3_nv(ctypes.byref(self.cfg))
+
+    @property
+    def ncell(self) -> int:
+        return self.cfg.nx
+
+    def zeros(self) -> np.ndarray:
+        return np.zeros((self.ncell, self.nv))
+
+
+def make_config3v(*, nx, x0=0.0, lx=1.0, nv=(8, 8, 8), vmin=(-1.0, -1.0, -1.0), vmax=(1.0, 1.0, 1.0),
+                  omega=0.5, dt=0.0, cfl=None, conservative=1, relax_exact=1,
+                  inflow=((1, 0, 0, 0, 1), (1, 0, 0, 0, 1))) -> Orc3Config:
+    c = Orc3Config()
+    c.nx, c.x0, c.lx = nx, x0, lx
+    c.nvx, c.nvy, c.nvz = nv
+    for k in range(3):
+        c.vmin[k], c.vmax[k] = vmin[k], vmax[k]
+    c.omega, c.conservative, c.relax_exact = omega, conservative, relax_exact
+    for s in range(2):
+        for k in range(5):
+            c.inflow[s][k] = inflow[s][k]
+    c.dt = dt if cfl is None else lib().orc3_dt_from_cfl(ctypes.byref(c), cfl)
+    return c
+
+
+def velocities3v(prob: Problem3v):
+    L, c = lib(), ctypes.byref(prob.cfg)
+    n = (prob.cfg.nvx, prob.cfg.nvy, prob.cfg.nvz)
+    return [np.array([L.orc3_c(c, a, j) for j in range(n[a])]) for a in range(3)]
+
+
+def maxwellian3v(prob: Problem3v, p) -> np.ndarray:
+    out = np.zeros(prob.nv)
+    lib().orc3_maxwellian(ctypes.byref(prob.cfg), _p(_vec(p)), _p(out))
+    return out
+
+
+def moments3v(prob: Problem3v, f) -> np.ndarray:
+    out = np.zeros(5)
+    lib().orc3_moments(ctypes.byref(prob.cfg), _p(np.ascontiguousarray(f, dtype=np.float64)), _p(out))
+    return out
+
+
+def state_moments3v(prob: Problem3v, f) -> np.ndarray:
+    return np.array([moments3v(prob, f[i]) for i in range(prob.ncell)])
+
+
+def effective_params3v(prob: Problem3v, q):
+    out = np.zeros(5)
+    it = lib().orc3_effective_params(ctypes.byref(prob.cfg), _p(_vec(q)), _p(out))
+    return it, out
+
+
+def init_step3v(prob: Problem3v, x_split, left, right) -> np.ndarray:
+    f = prob.zeros()
+    lib().orc3_init_step(ctypes.byref(prob.cfg), x_split, _p(_vec(left)), _p(_vec(right)), _p(f))
+    return f
+
+
+def stream3v(prob: Problem3v, f) -> np.ndarray:
+    ft = prob.zeros()
+    lib().orc3_stream(ctypes.byref(prob.cfg), _p(np.ascontiguousarray(f)), _p(ft))
+    return ft
+
+
+def relax3v(prob: Problem3v, f):
+    f = np.array(f, dtype=np.float64, copy=True)
+    mom = np.zeros((prob.ncell, 5))
+    if lib().orc3_relax(ctypes.byref(prob.cfg), _p(f), _p(mom)) != 0:
+        raise RuntimeError("oracle relaxation failed")
+    return f, mom
+
+
+def step3v(prob: Problem3v, f, nsteps: int):
+    f = np.array(f, dtype=np.float64, copy=True)
+    mom = np.zeros((prob.ncell, 5))
+    if lib().orc3_step(ctypes.byref(prob.cfg), _p(f), nsteps, _p(mom)) != 0:
+        raise RuntimeError("oracle step failed")
+    return f, mom
+
+
+def shock3v_problem(*, mach, nx, length, nv, vx, vt, omega, dt, steps=0, conservative=1, relax_exact=1,
+                    **_ignored) -> tuple[Problem3v, np.ndarray]:
+    """Sec. 4.1 as the paper computed it: domain [-L/2, L/2], full velocity grid
+    nv = (N_vx, N_vy, N_vz) on vx x vt x vt, fixed time step, Rankine-Hugoniot
+    inflow states, step profile at x = 0.  Returns (problem, f0)."""
+    up, down = rankine_hugoniot(mach)
+    u5 = (up[0], up[1], 0.0, 0.0, up[3])
+    d5 = (down[0], down[1], 0.0, 0.0, down[3])
+    cfg = make_config3v(nx=nx, x0=-0.5 * length, lx=length, nv=nv, vmin=(vx[0], vt[0], vt[0]),
+                        vmax=(vx[1], vt[1], vt[1]), omega=omega, dt=dt, conservative=conservative,
+                        relax_exact=relax_exact, inflow=(u5, d5))
+    prob = Problem3v(cfg, steps, {"up": u5, "down": d5})
+    return prob, init_step3v(prob, 0.0, u5, d5)
