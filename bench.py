@@ -540,6 +540,107 @@ def adjoint_arm(args, world, rank, local, pg):
     s.close()
 
 
+# Full velocity grid (1D space): per update (one f value at one (cell,
+# velocity) point) read f^n once and write f^{n+1} once (16 B); FP64 flops:
+# streaming 3, the five moment sums 9, relaxation b f~ + px py pz 4.
+FLOPS_PER_UPDATE_3V = 16.0
+BYTES_PER_UPDATE_3V = 16.0
+
+
+def shock3v_arm(args, w, world, rank, local, pg):
+    """The shock of Sec. 4.1 as the paper computed it (full 3D velocity grid);
+    a benchmark step is the workload's time steps from the step profile."""
+    import torch
+
+    import oracle
+    from paper_0903_4044_gb300 import bgk as B
+    from paper_0903_4044_gb300 import build, solver
+
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    s = solver.make_shock3v(w, stream=stream.cuda_stream)
+    ncell, nv, nsteps = s.ncell, s.nv, w["steps"]
+    f0_host = torch.empty((ncell, nv), dtype=torch.float64, pin_memory=True)
+    B.bgk3v_get_state(s.h, f0_host.numpy())
+    f0_dev = f0_host.to(f"cuda:{local}")
+    mom_host = torch.empty((ncell, 5), dtype=torch.float64, pin_memory=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    def one_step(ev=None):
+        B.bgk3v_set_state(s.h, f0_dev)
+        if ev is not None:
+            ev[0].record(stream)
+        B.bgk3v_step(s.h, nsteps)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize()
+    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(pg)
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for k in range(args.steps):
+            flush.zero_()
+            one_step(pairs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+    B.bgk3v_sync(s.h)
+    elapsed = max_over_ranks(pg, t_start.elapsed_time(t_end) / 1e3)
+    per_launch = sum(a.elapsed_time(b) for a, b in pairs) / 1e3 / (args.steps * nsteps)
+    updates = ncell * nv * nsteps
+    value = world * updates * args.steps / elapsed
+    e2e = None
+    if not args.no_e2e:
+        def e2e_step():
+            B.bgk3v_set_state(s.h, f0_host.numpy())
+            B.bgk3v_step(s.h, nsteps)
+            B.bgk3v_moments(s.h, mom_host.numpy(), 0)
+        e2e_step()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+        e2e = {"value": world * updates * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(f0_host.numel() * 8), "d2h_bytes_per_step": int(mom_host.numel() * 8)}
+    peaks = load_peaks()
+    alu = FLOPS_PER_UPDATE_3V * ncell * nv / per_launch / 1e12
+    hbm = BYTES_PER_UPDATE_3V * ncell * nv / per_launch / 1e9
+    roof = {"bound": "alu", "achieved": alu, "peak": FP64_NOMINAL_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": alu / (FP64_NOMINAL_FLOPS / 1e12), "traffic": args.traffic,
+            "peak_source": "nominal FP64 (unit counts x clock)", "kernel": "bgk::step3v_kernel",
+            "launch_ms": per_launch * 1e3, "hbm_gbs": hbm, "hbm_frac": hbm / peaks["hbm_gbs"]}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle.build()
+        sample = max(1, int(2e9 // (ncell * nv)))  # about 10 s on the host cores
+        prob, f = oracle.shock3v_problem(**w)
+        t0 = time.perf_counter()
+        oracle.step3v(prob, f, sample)
+        dt = time.perf_counter() - t0
+        cpu = {"value": ncell * nv * sample / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"{sample} time steps of {w['name']} ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "cells": ncell, "velocities": nv, "time_steps": nsteps,
+                       "max_courant": s.info.max_courant, "parallelism": f"replica x{world}",
+                       "l2": "flushed (256 MB write) between timed steps; state larger than L2"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": args.steps * nsteps,
+        }), flush=True)
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -561,9 +662,19 @@ def main():
     ap.add_argument("--checkpoint-every", type=int, default=100, help="adjoint workload: steps per checkpoint")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
-    w = workload(args.workload) if args.workload not in ("batch", "adjoint") else None
+    w = workload(args.workload) if args.workload not in ("batch", "adjoint", "shock3v", "shock3v_m15") else None
     if args.time_steps is not None and w is not None:
         w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
+    if args.workload in ("shock3v", "shock3v_m15") and args.impl != "reference":
+        from paper_0903_4044_gb300 import workloads as W
+
+        w3 = W.SHOCK3V_M3 if args.workload == "shock3v" else W.SHOCK3V_M15
+        if args.time_steps is not None:
+            w3 = dict(w3, steps=args.time_steps, name=f"{w3['name']}_{args.time_steps}steps")
+        shock3v_arm(args, w3, world, rank, local, pg)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
     if args.workload in ("batch", "adjoint"):
         (batch_arm if args.workload == "batch" else adjoint_arm)(args, world, rank, local, pg)
         if pg is not None:

@@ -236,6 +236,66 @@ BGK_API bgk_status bgk_autotune(bgk_solver* s, int trial_steps, int* tile_out);
  * velocity grid, precision) share one tuning run. */
 BGK_API bgk_status bgk_batch_autotune(bgk_batch* b, int trial_steps);
 
+/* ---- full three-dimensional velocity grid ------------------------------- */
+
+/* The normal shock of Sec. 4.1 as the paper computed it: one spatial
+ * dimension and the full velocity grid (the Chu reduction is not made), so
+ * the state of a spatial cell is f on N_vx x N_vy x N_vz velocity cells.
+ * Streaming along x uses the integer shift of Eq. (exact) and the upwind
+ * remainder of Eq. (upwind) (any Courant number); the relaxation target is
+ * the 3D Maxwellian of Eq. (Maxw), Phi = n (pi theta)^(-3/2)
+ * exp(-|c - U|^2 / theta), from effective parameters when conservative.
+ * FP64 only.
+ *
+ * STATE LAYOUT (3V): f[cell][v], v = (jz * nvy + jy) * nvx + jx, one double
+ * per point; c_a = vmin[a] + (j_a + 1/2) (vmax[a] - vmin[a]) / nv_a.
+ * Moments: (n, ux, uy, uz, theta) per cell. */
+typedef struct {
+  int32_t nx;                 /* spatial cells on [x0, x0 + lx] */
+  int32_t nvx, nvy, nvz;      /* velocity cells per component (each 1..256) */
+  int32_t conservative;       /* 1: effective Maxwellian parameters (exact conservation) */
+  int32_t relax_exact;        /* 1: Eq. (relaxation); 0: f += dt nu (Phi - f) */
+  int32_t reserved0, reserved1; /* must be 0 */
+  double x0, lx;
+  double vmin[3], vmax[3];    /* velocity box per component */
+  double omega;               /* nu = n theta^(1 - omega) */
+  double dt;                  /* time step; 0 = derive from cfl */
+  double cfl;                 /* max|c_x| dt / dx when dt = 0 */
+  double inflow[2][5];        /* (n, ux, uy, uz, theta) held beyond XLO and XHI */
+  void* cuda_stream;          /* cudaStream_t; NULL = legacy default stream */
+} bgk3v_config;
+
+typedef struct {
+  double dt, dx, dv;          /* dv = dc_x dc_y dc_z */
+  double max_courant;         /* max |c_x| dt / dx (may exceed 1) */
+  int64_t ncell, nv;
+  int64_t steps_done;
+  int64_t device_bytes;
+} bgk3v_info;
+
+typedef struct bgk3v_solver bgk3v_solver;
+
+/* Validate (before any CUDA call), build tables, allocate two state buffers.
+ * Errors: INVALID_ARG, UNSUPPORTED (more than 2^24 velocities per cell or a
+ * component above 256 cells), OOM, CUDA. */
+BGK_API bgk_status bgk3v_create(const bgk3v_config* cfg, bgk3v_solver** out);
+BGK_API bgk_status bgk3v_destroy(bgk3v_solver* s);
+BGK_API bgk_status bgk3v_get_info(const bgk3v_solver* s, bgk3v_info* out);
+/* Step profile: Maxwellian of left (n, ux, uy, uz, theta) for x < x_split,
+ * of right beyond.  Enqueued; resets steps_done and the error flag. */
+BGK_API bgk_status bgk3v_init_step(bgk3v_solver* s, double x_split, const double left[5], const double right[5]);
+/* Copy a state (STATE LAYOUT (3V), ncell*nv doubles) in or out; get
+ * synchronises. */
+BGK_API bgk_status bgk3v_set_state(bgk3v_solver* s, const double* f, int on_device);
+BGK_API bgk_status bgk3v_get_state(bgk3v_solver* s, double* f, int on_device);
+/* Enqueue nsteps steps (one kernel per step).  Asynchronous. */
+BGK_API bgk_status bgk3v_step(bgk3v_solver* s, int64_t nsteps);
+/* mom[cell][5] = (n, ux, uy, uz, theta): which = 0 of the current state,
+ * which = 1 of the last step's post-streaming state.  Synchronises. */
+BGK_API bgk_status bgk3v_moments(bgk3v_solver* s, int which, double* mom, int on_device);
+/* Wait for the stream; BGK_ERR_NUMERIC if a cell failed. */
+BGK_API bgk_status bgk3v_sync(bgk3v_solver* s);
+
 /* ---- adjoint -------------------------------------------------------------- */
 
 /* Gradient of the lid-integrated shear by the adjoint of the split step.

@@ -29,6 +29,8 @@ EXPORTS = (
     "bgk_rankine_hugoniot", "bgk_last_error", "bgk_status_string", "bgk_abi_version",
     "bgk_step_noalloc", "bgk_batch_create", "bgk_batch_solver", "bgk_batch_step", "bgk_batch_sync",
     "bgk_batch_destroy", "bgk_autotune", "bgk_batch_autotune", "bgk_adjoint_lid_shear",
+    "bgk3v_create", "bgk3v_destroy", "bgk3v_get_info", "bgk3v_init_step", "bgk3v_set_state",
+    "bgk3v_get_state", "bgk3v_step", "bgk3v_moments", "bgk3v_sync",
 )
 
 
@@ -68,8 +70,25 @@ class bgk_info(ctypes.Structure):
 
 
 _lib = None
+class bgk3v_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("nvx", ctypes.c_int32), ("nvy", ctypes.c_int32),
+                ("nvz", ctypes.c_int32), ("conservative", ctypes.c_int32), ("relax_exact", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("x0", ctypes.c_double), ("lx", ctypes.c_double),
+                ("vmin", ctypes.c_double * 3), ("vmax", ctypes.c_double * 3),
+                ("omega", ctypes.c_double), ("dt", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("inflow", (ctypes.c_double * 5) * 2), ("cuda_stream", ctypes.c_void_p)]
+
+
+class bgk3v_info(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("dx", ctypes.c_double), ("dv", ctypes.c_double),
+                ("max_courant", ctypes.c_double), ("ncell", ctypes.c_int64), ("nv", ctypes.c_int64),
+                ("steps_done", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _D4 = ctypes.c_double * 4
+_D5 = ctypes.c_double * 5
 
 
 def lib() -> ctypes.CDLL:
@@ -104,6 +123,15 @@ def lib() -> ctypes.CDLL:
             "bgk_autotune": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "bgk_batch_autotune": ([_P, ctypes.c_int], ctypes.c_int),
             "bgk_adjoint_lid_shear": ([_P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int, _D4], ctypes.c_int),
+            "bgk3v_create": ([ctypes.POINTER(bgk3v_config), ctypes.POINTER(_P)], ctypes.c_int),
+            "bgk3v_destroy": ([_P], ctypes.c_int),
+            "bgk3v_get_info": ([_P, ctypes.POINTER(bgk3v_info)], ctypes.c_int),
+            "bgk3v_init_step": ([_P, ctypes.c_double, _D5, _D5], ctypes.c_int),
+            "bgk3v_set_state": ([_P, _P, ctypes.c_int], ctypes.c_int),
+            "bgk3v_get_state": ([_P, _P, ctypes.c_int], ctypes.c_int),
+            "bgk3v_step": ([_P, ctypes.c_int64], ctypes.c_int),
+            "bgk3v_moments": ([_P, ctypes.c_int, _P, ctypes.c_int], ctypes.c_int),
+            "bgk3v_sync": ([_P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -274,3 +302,66 @@ def bgk_adjoint_lid_shear(h: int, nsteps: int, checkpoint_every: int, grad_out=N
     addr, dev = _ptr(grad_out) if grad_out is not None else (None, 0)
     _check(lib().bgk_adjoint_lid_shear(h, nsteps, checkpoint_every, addr, dev, out), "bgk_adjoint_lid_shear")
     return out[0], out[1], out[2]
+
+
+# --- full 3D velocity grid, one spatial dimension -------------------------
+def make_config3v(*, nx, x0=0.0, lx=1.0, nv=(8, 8, 8), vmin=(-1.0, -1.0, -1.0), vmax=(1.0, 1.0, 1.0),
+                  omega=0.5, dt=0.0, cfl=0.0, conservative=1, relax_exact=1,
+                  inflow=((1, 0, 0, 0, 1), (1, 0, 0, 0, 1)), stream=None) -> bgk3v_config:
+    """Fill a bgk3v_config; inflow = ((n, ux, uy, uz, theta) at XLO, at XHI)."""
+    c = bgk3v_config()
+    c.nx = nx
+    c.nvx, c.nvy, c.nvz = nv
+    c.conservative, c.relax_exact = conservative, relax_exact
+    c.x0, c.lx = x0, lx
+    for k in range(3):
+        c.vmin[k], c.vmax[k] = vmin[k], vmax[k]
+    c.omega, c.dt, c.cfl = omega, dt, cfl
+    for e in range(2):
+        for k in range(5):
+            c.inflow[e][k] = inflow[e][k]
+    c.cuda_stream = stream
+    return c
+
+
+def bgk3v_create(cfg: bgk3v_config) -> int:
+    h = _P()
+    _check(lib().bgk3v_create(ctypes.byref(cfg), ctypes.byref(h)), "bgk3v_create")
+    return h.value
+
+
+def bgk3v_destroy(h: int) -> None:
+    _check(lib().bgk3v_destroy(h), "bgk3v_destroy")
+
+
+def bgk3v_get_info(h: int) -> bgk3v_info:
+    info = bgk3v_info()
+    _check(lib().bgk3v_get_info(h, ctypes.byref(info)), "bgk3v_get_info")
+    return info
+
+
+def bgk3v_init_step(h: int, x_split: float, left, right) -> None:
+    _check(lib().bgk3v_init_step(h, x_split, _D5(*left), _D5(*right)), "bgk3v_init_step")
+
+
+def bgk3v_set_state(h: int, f) -> None:
+    addr, dev = _ptr(f)
+    _check(lib().bgk3v_set_state(h, addr, dev), "bgk3v_set_state")
+
+
+def bgk3v_get_state(h: int, out) -> None:
+    addr, dev = _ptr(out)
+    _check(lib().bgk3v_get_state(h, addr, dev), "bgk3v_get_state")
+
+
+def bgk3v_step(h: int, nsteps: int) -> None:
+    _check(lib().bgk3v_step(h, nsteps), "bgk3v_step")
+
+
+def bgk3v_moments(h: int, out, which: int = 0) -> None:
+    addr, dev = _ptr(out)
+    _check(lib().bgk3v_moments(h, which, addr, dev), "bgk3v_moments")
+
+
+def bgk3v_sync(h: int) -> None:
+    _check(lib().bgk3v_sync(h), "bgk3v_sync")

@@ -1274,3 +1274,282 @@ extern "C" bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int c
   return check_flag(s);
   BGK_GUARD_END
 }
+
+// ---------------------------------------------------------------------------
+// Full 3D velocity grid, one spatial dimension (kernels in bgk_step3v.cu).
+// ---------------------------------------------------------------------------
+struct bgk3v_solver {
+  bgk3v_config cfg;
+  bgk::Params3v P;
+  bgk::Inflow3v inflow;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  double* mom_step = nullptr;  // [ncell][5] of the last post-streaming state
+  double* mom_tmp = nullptr;
+  double* c[3] = {nullptr, nullptr, nullptr};
+  double* cc = nullptr;
+  int* shift = nullptr;
+  int* upwind = nullptr;
+  double* rem = nullptr;
+  double* ghost = nullptr;
+  int* err = nullptr;
+  int64_t steps_done = 0;
+  int64_t device_bytes = 0;
+  double max_courant = 0.0;
+  bgk::Tables3v tables() const {
+    bgk::Tables3v T;
+    T.c[0] = c[0];
+    T.c[1] = c[1];
+    T.c[2] = c[2];
+    T.c2 = cc;
+    T.shift = shift;
+    T.upwind = upwind;
+    T.rem = rem;
+    T.ghost = ghost;
+    return T;
+  }
+  size_t state_elems() const { return (size_t)P.nx * P.nv; }
+};
+
+namespace {
+
+void release3v(bgk3v_solver* s) {
+  if (!s) return;
+  void* bufs[] = {s->f[0], s->f[1], s->mom_step, s->mom_tmp, s->c[0], s->c[1], s->c[2], s->cc,
+                  s->shift, s->upwind, s->rem, s->ghost, s->err};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete s;
+}
+
+bgk_status validate3v(const bgk3v_config* c, bgk::Params3v& p, double* max_courant) {
+  if (c->nx < 1) return fail(BGK_ERR_INVALID_ARG, "nx must be >= 1");
+  const int n3[3] = {c->nvx, c->nvy, c->nvz};
+  for (int a = 0; a < 3; ++a) {
+    if (n3[a] < 1) return fail(BGK_ERR_INVALID_ARG, "velocity cell counts must be >= 1");
+    if (n3[a] > 256) return fail(BGK_ERR_UNSUPPORTED, "at most 256 velocity cells per component (got %d)", n3[a]);
+    if (!std::isfinite(c->vmin[a]) || !std::isfinite(c->vmax[a]) || !(c->vmax[a] > c->vmin[a]))
+      return fail(BGK_ERR_INVALID_ARG, "velocity box component %d must have vmax > vmin", a);
+  }
+  const long long nv = (long long)c->nvx * c->nvy * c->nvz;
+  if (nv > (1LL << 24)) return fail(BGK_ERR_UNSUPPORTED, "%lld velocities per cell (max 2^24)", nv);
+  if (!std::isfinite(c->x0) || !std::isfinite(c->lx) || !(c->lx > 0.0))
+    return fail(BGK_ERR_INVALID_ARG, "lx must be finite and > 0");
+  if (!std::isfinite(c->omega)) return fail(BGK_ERR_INVALID_ARG, "omega must be finite");
+  if (c->conservative != 0 && c->conservative != 1) return fail(BGK_ERR_INVALID_ARG, "conservative must be 0 or 1");
+  if (c->relax_exact != 0 && c->relax_exact != 1) return fail(BGK_ERR_INVALID_ARG, "relax_exact must be 0 or 1");
+  if (c->reserved0 != 0 || c->reserved1 != 0) return fail(BGK_ERR_INVALID_ARG, "reserved fields must be 0");
+  for (int e = 0; e < 2; ++e) {
+    const double* st = c->inflow[e];
+    for (int k = 0; k < 5; ++k)
+      if (!std::isfinite(st[k])) return fail(BGK_ERR_INVALID_ARG, "inflow state %d is not finite", e);
+    if (!(st[0] > 0.0) || !(st[4] > 0.0)) return fail(BGK_ERR_INVALID_ARG, "inflow state %d needs n > 0 and theta > 0", e);
+  }
+  p.nx = c->nx;
+  p.nvx = c->nvx;
+  p.nvy = c->nvy;
+  p.nvz = c->nvz;
+  p.nv = (int)nv;
+  p.conservative = c->conservative;
+  p.relax_exact = c->relax_exact;
+  p.x0 = c->x0;
+  p.dx = c->lx / c->nx;
+  p.omega = c->omega;
+  double mx = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    p.dc[a] = (c->vmax[a] - c->vmin[a]) / n3[a];
+    p.vmin[a] = c->vmin[a];
+  }
+  for (int j = 0; j < c->nvx; ++j) mx = std::max(mx, std::fabs(c->vmin[0] + (j + 0.5) * p.dc[0]));
+  p.dv = p.dc[0] * p.dc[1] * p.dc[2];
+  if (c->dt > 0.0 && std::isfinite(c->dt)) {
+    p.dt = c->dt;
+  } else if (c->dt == 0.0 && c->cfl > 0.0 && std::isfinite(c->cfl) && mx > 0.0) {
+    p.dt = c->cfl * p.dx / mx;
+  } else {
+    return fail(BGK_ERR_INVALID_ARG, "need dt > 0, or dt = 0 and cfl > 0");
+  }
+  *max_courant = mx * p.dt / p.dx;
+  if (*max_courant > 1e6) return fail(BGK_ERR_UNSUPPORTED, "Courant number %.3g is too large", *max_courant);
+  return BGK_OK;
+}
+
+template <typename T>
+cudaError_t dev_alloc3(bgk3v_solver* s, T** p, size_t count) {
+  const size_t bytes = sizeof(T) * (count ? count : 1);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess) s->device_bytes += (int64_t)bytes;
+  return e;
+}
+
+bgk_status check_flag3v(bgk3v_solver* s) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  if (h & bgk::ERR_MOMENT) return fail(BGK_ERR_NUMERIC, "a cell reached n <= 0, theta <= 0 or a non-finite moment");
+  if (h & bgk::ERR_EFFECTIVE)
+    return fail(BGK_ERR_NUMERIC, "the effective-parameter iteration did not converge in a cell");
+  return BGK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bgk_status bgk3v_create(const bgk3v_config* cfg, bgk3v_solver** out) {
+  BGK_GUARD_BEGIN
+  if (!out) return fail(BGK_ERR_INVALID_ARG, "null output");
+  *out = nullptr;
+  if (!cfg) return fail(BGK_ERR_INVALID_ARG, "null config");
+  bgk::Params3v P{};
+  double mc = 0.0;
+  bgk_status st = validate3v(cfg, P, &mc);
+  if (st != BGK_OK) return st;
+  bgk3v_solver* s = new bgk3v_solver();
+  s->cfg = *cfg;
+  s->P = P;
+  s->max_courant = mc;
+  s->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  for (int e = 0; e < 2; ++e)
+    for (int k = 0; k < 5; ++k) s->inflow.s[e][k] = cfg->inflow[e][k];
+  cudaError_t e = cudaGetDevice(&s->device);
+  const size_t n = s->state_elems();
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->f[0], n);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->f[1], n);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->mom_step, (size_t)P.nx * 5);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->mom_tmp, (size_t)P.nx * 5);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->c[0], (size_t)P.nvx);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->c[1], (size_t)P.nvy);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->c[2], (size_t)P.nvz);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->cc, (size_t)P.nv);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->shift, (size_t)P.nvx);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->upwind, (size_t)P.nvx);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->rem, (size_t)P.nvx);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->ghost, 2 * (size_t)P.nv);
+  if (e == cudaSuccess) e = dev_alloc3(s, &s->err, 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->f[0], 0, sizeof(double) * n, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->mom_step, 0, sizeof(double) * P.nx * 5, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess)
+    e = bgk::launch_tables3v(P, s->c[0], s->c[1], s->c[2], s->cc, s->shift, s->upwind, s->rem, s->ghost, s->inflow,
+                             s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    release3v(s);
+    return cuda_fail(e, "bgk3v_create");
+  }
+  *out = s;
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk3v_destroy(bgk3v_solver* s) {
+  if (!s) return BGK_OK;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  release3v(s);
+  return BGK_OK;
+}
+
+bgk_status bgk3v_get_info(const bgk3v_solver* s, bgk3v_info* out) {
+  if (!s || !out) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  out->dt = s->P.dt;
+  out->dx = s->P.dx;
+  out->dv = s->P.dv;
+  out->max_courant = s->max_courant;
+  out->ncell = s->P.nx;
+  out->nv = s->P.nv;
+  out->steps_done = s->steps_done;
+  out->device_bytes = s->device_bytes;
+  return BGK_OK;
+}
+
+bgk_status bgk3v_init_step(bgk3v_solver* s, double x_split, const double left[5], const double right[5]) {
+  BGK_GUARD_BEGIN
+  if (!s || !left || !right) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < 5; ++k)
+    if (!std::isfinite(left[k]) || !std::isfinite(right[k])) return fail(BGK_ERR_INVALID_ARG, "non-finite state");
+  if (!(left[0] > 0.0) || !(left[4] > 0.0) || !(right[0] > 0.0) || !(right[4] > 0.0))
+    return fail(BGK_ERR_INVALID_ARG, "states need n > 0 and theta > 0");
+  if (cudaSetDevice(s->device) != cudaSuccess) return fail(BGK_ERR_CUDA, "cudaSetDevice");
+  bgk::Inflow3v lr;
+  for (int k = 0; k < 5; ++k) {
+    lr.s[0][k] = left[k];
+    lr.s[1][k] = right[k];
+  }
+  s->cur = 0;
+  s->steps_done = 0;
+  cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess) e = bgk::launch_init3v(s->P, s->tables(), x_split, lr, s->f[0], s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bgk3v_init_step");
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
+bgk_status bgk3v_set_state(bgk3v_solver* s, const double* f, int on_device) {
+  if (!s || !f) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  if (cudaSetDevice(s->device) != cudaSuccess) return fail(BGK_ERR_CUDA, "cudaSetDevice");
+  s->cur = 0;
+  s->steps_done = 0;
+  cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->f[0], f, sizeof(double) * s->state_elems(),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bgk3v_set_state");
+  return BGK_OK;
+}
+
+bgk_status bgk3v_get_state(bgk3v_solver* s, double* f, int on_device) {
+  if (!s || !f) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  if (cudaSetDevice(s->device) != cudaSuccess) return fail(BGK_ERR_CUDA, "cudaSetDevice");
+  cudaError_t e = cudaMemcpyAsync(f, s->f[s->cur], sizeof(double) * s->state_elems(),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bgk3v_get_state");
+  return BGK_OK;
+}
+
+bgk_status bgk3v_step(bgk3v_solver* s, int64_t nsteps) {
+  if (!s) return fail(BGK_ERR_INVALID_ARG, "null solver");
+  if (nsteps < 0) return fail(BGK_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return BGK_OK;
+  if (cudaSetDevice(s->device) != cudaSuccess) return fail(BGK_ERR_CUDA, "cudaSetDevice");
+  const bgk::Tables3v T = s->tables();
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const cudaError_t e = bgk::launch_step3v(s->P, T, s->f[s->cur], s->f[s->cur ^ 1], s->mom_step, s->err, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bgk3v_step");
+    s->cur ^= 1;
+    ++s->steps_done;
+  }
+  return BGK_OK;
+}
+
+bgk_status bgk3v_moments(bgk3v_solver* s, int which, double* mom, int on_device) {
+  if (!s || !mom) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  if (which != 0 && which != 1) return fail(BGK_ERR_INVALID_ARG, "which must be 0 or 1");
+  if (cudaSetDevice(s->device) != cudaSuccess) return fail(BGK_ERR_CUDA, "cudaSetDevice");
+  cudaError_t e = cudaSuccess;
+  const double* src = s->mom_step;
+  if (which == 0) {
+    e = bgk::launch_moments3v(s->P, s->tables(), s->f[s->cur], s->mom_tmp, s->stream);
+    src = s->mom_tmp;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(mom, src, sizeof(double) * s->P.nx * 5,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bgk3v_moments");
+  return BGK_OK;
+}
+
+bgk_status bgk3v_sync(bgk3v_solver* s) {
+  if (!s) return fail(BGK_ERR_INVALID_ARG, "null solver");
+  if (cudaSetDevice(s->device) != cudaSuccess) return fail(BGK_ERR_CUDA, "cudaSetDevice");
+  return check_flag3v(s);
+}
+
+}  // extern "C"

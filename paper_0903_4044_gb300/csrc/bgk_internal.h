@@ -90,6 +90,33 @@ cudaError_t launch_build_mixed_tables(const Params& P, const Tables& T, const Mi
                                       cudaStream_t stream);
 size_t step_mixed_smem_bytes(const Params& P, int tile, int prec);
 int mixed_groups_per_lane(const Params& P, int tile);
+// Full 3D velocity grid, one spatial dimension (bgk_step3v.cu).
+struct Params3v {
+  int nx, nvx, nvy, nvz, nv;
+  int conservative, relax_exact;
+  double x0, dx, dt, dv, omega;
+  double dc[3], vmin[3];
+};
+struct Tables3v {
+  const double* c[3];    // [nvx], [nvy], [nvz] velocity-cell centres
+  const double* c2;      // [nv] |c|^2
+  const int* shift;      // [nvx] [C], C = c_x dt/dx, toward zero
+  const int* upwind;     // [nvx] +1 for C > 0, else -1
+  const double* rem;     // [nvx] |C - [C]|
+  const double* ghost;   // [2][nv] inflow Maxwellians at XLO, XHI
+};
+struct Inflow3v {
+  double s[2][5];  // (n, ux, uy, uz, theta)
+};
+cudaError_t launch_tables3v(const Params3v& P, double* c0, double* c1, double* c2, double* cc, int* shift,
+                            int* upwind, double* rem, double* ghost, const Inflow3v& inflow, cudaStream_t stream);
+cudaError_t launch_init3v(const Params3v& P, const Tables3v& T, double x_split, const Inflow3v& lr, double* f,
+                          cudaStream_t stream);
+cudaError_t launch_step3v(const Params3v& P, const Tables3v& T, const double* fin, double* fout, double* mom,
+                          int* err, cudaStream_t stream);
+cudaError_t launch_moments3v(const Params3v& P, const Tables3v& T, const double* f, double* mom,
+                             cudaStream_t stream);
+
 // Reverse pass of the lid shear (bgk_adjoint.cu).
 cudaError_t launch_adj_lid_table(const Params& P, const Tables& T, double2* dghost, double* demit,
                                  cudaStream_t stream);

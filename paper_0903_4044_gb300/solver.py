@@ -195,3 +195,80 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Solver3v:
+    """Owns one ``bgk3v_solver`` (full 3D velocity grid, one spatial dimension)."""
+
+    def __init__(self, cfg: B.bgk3v_config):
+        self.cfg = cfg
+        self.h = B.bgk3v_create(cfg)
+        self.info = B.bgk3v_get_info(self.h)
+        self.ncell = int(self.info.ncell)
+        self.nv = int(self.info.nv)
+
+    def close(self) -> None:
+        if self.h:
+            B.bgk3v_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_step(self, x_split, left, right) -> None:
+        B.bgk3v_init_step(self.h, x_split, left, right)
+
+    def set_state(self, f) -> None:
+        B.bgk3v_set_state(self.h, f)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((self.ncell, self.nv))
+        B.bgk3v_get_state(self.h, out)
+        return out
+
+    def step(self, n: int) -> None:
+        B.bgk3v_step(self.h, n)
+
+    def sync(self) -> None:
+        B.bgk3v_sync(self.h)
+
+    def moments(self, which: int = 0, out=None):
+        if out is None:
+            out = np.empty((self.ncell, 5))
+        B.bgk3v_moments(self.h, out, which)
+        return out
+
+    @property
+    def dt(self) -> float:
+        return self.info.dt
+
+
+def shock3v_config(*, mach, nx, length, nv, vx, vt, omega, dt, conservative=1, relax_exact=1, stream=None,
+                   **_ignored):
+    """(cfg, up, down) for the Sec. 4.1 shock on the full velocity grid
+    nv = (N_vx, N_vy, N_vz) over vx x vt x vt with a fixed time step."""
+    up4, down4 = B.bgk_rankine_hugoniot(mach, GAMMA)
+    up = (up4[0], up4[1], 0.0, 0.0, up4[3])
+    down = (down4[0], down4[1], 0.0, 0.0, down4[3])
+    cfg = B.make_config3v(nx=nx, x0=-0.5 * length, lx=length, nv=nv, vmin=(vx[0], vt[0], vt[0]),
+                          vmax=(vx[1], vt[1], vt[1]), omega=omega, dt=dt, conservative=conservative,
+                          relax_exact=relax_exact, inflow=(up, down), stream=stream)
+    return cfg, up, down
+
+
+def make_shock3v(w: dict, stream=None, **over) -> Solver3v:
+    cfg, up, down = shock3v_config(**{**w, **over}, stream=stream)
+    s = Solver3v(cfg)
+    s.init_step(0.0, up, down)
+    s.up, s.down = up, down
+    return s

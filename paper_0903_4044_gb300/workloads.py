@@ -63,7 +63,18 @@ CAVITY_128 = dict(
     n=128, nv=32, vbox=(-5.0, 5.0), omega=0.5, cfl=0.5, steps=2000, seed=0, amp=1e-3,
 )
 
-WORKLOADS = {w["name"]: w for w in (SHOCK_M2, CAVITY_64, CAVITY_256, CAVITY_128)}
+# The shock as the paper computed it (Sec. 4.1): full velocity grid, no Chu
+# reduction, omega 0.74, domain 70 mean free paths, dt 0.05.
+SHOCK3V_M15 = dict(
+    name="shock3v_m1.5_nx512_v16x16x16", kind="shock3v", mach=1.5, nx=512, length=70.0,
+    nv=(16, 16, 16), vx=(-5.0, 7.0), vt=(-6.0, 6.0), omega=0.74, dt=0.05, steps=400,
+)
+SHOCK3V_M3 = dict(
+    name="shock3v_m3_nx2048_v30x30x30", kind="shock3v", mach=3.0, nx=2048, length=70.0,
+    nv=(30, 30, 30), vx=(-10.0, 12.0), vt=(-11.0, 11.0), omega=0.74, dt=0.05, steps=100,
+)
+
+WORKLOADS = {w["name"]: w for w in (SHOCK_M2, CAVITY_64, CAVITY_256, CAVITY_128, SHOCK3V_M15, SHOCK3V_M3)}
 
 
 def scaled(w: dict, **over) -> dict:

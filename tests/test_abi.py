@@ -23,7 +23,7 @@ def L():
 
 def _declared(header: str) -> set[str]:
     text = open(os.path.join(ROOT, "include", header)).read()
-    return set(re.findall(r"^BGK_API\s+[^;(]*?\b(bgk_\w+)\s*\(", text, flags=re.M))
+    return set(re.findall(r"^BGK_API\s+[^;(]*?\b(bgk\w+)\s*\(", text, flags=re.M))
 
 
 def test_exports_every_declared_symbol(L):
