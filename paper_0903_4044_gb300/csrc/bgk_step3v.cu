@@ -14,8 +14,9 @@
 //           with the Gaussian factored per axis: warp a of the first three
 //           evaluates axis a's 1D factor and its sums, the three warps
 //           synchronise on a named barrier;
-//   pass 2  f~ again (its sources are still on chip) and
-//           f^{n+1} = b f~ + a Phi, Phi = px[jx] py[jy] pz[jz].
+//   pass 2  f^{n+1} = b f~ + a Phi, Phi = px[jx] py[jy] pz[jz], on the f~
+//           values pass 1 parked in the cell's output slots (each thread
+//           rereads its own writes, from L2).
 #include "bgk_device.cuh"
 
 namespace bgk {
@@ -96,11 +97,14 @@ __global__ void __launch_bounds__(kT) step3v_kernel(const Params3v P, const Tabl
   const int i = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // pass 1: stream and the five sums of Eq. (macroscopic)
+  // pass 1: stream (f~ parked in the cell's output slots) and the five sums
+  // of Eq. (macroscopic)
+  double* fo = fout + (size_t)i * P.nv;
   double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int j = threadIdx.x; j < P.nv; j += kT) {
     const Idx3 k = split3(P, j);
     const double ft = stream3(P, T, fin, i, j, k.jx);
+    fo[j] = ft;
     acc[0] += ft;
     acc[1] = fma(T.c[0][k.jx], ft, acc[1]);
     acc[2] = fma(T.c[1][k.jy], ft, acc[2]);
@@ -185,17 +189,15 @@ __global__ void __launch_bounds__(kT) step3v_kernel(const Params3v P, const Tabl
   }
   __syncthreads();
 
-  // pass 2: f^{n+1} = b f~ + a Phi
+  // pass 2: f^{n+1} = b f~ + a Phi, each thread on the f~ values it parked
   const double b = s_ab[1];
-  const bool ok = s_ok != 0;
   const double* px = fac;
   const double* py = fac + P.nvx;
   const double* pz = py + P.nvy;
-  double* fo = fout + (size_t)i * P.nv;
+  if (s_ok == 0) return;  // f^{n+1} = f~ (flagged)
   for (int j = threadIdx.x; j < P.nv; j += kT) {
     const Idx3 k = split3(P, j);
-    const double ft = stream3(P, T, fin, i, j, k.jx);
-    fo[j] = ok ? fma(b, ft, px[k.jx] * py[k.jy] * pz[k.jz]) : ft;
+    fo[j] = fma(b, fo[j], px[k.jx] * py[k.jy] * pz[k.jz]);
   }
 }
 
