@@ -103,6 +103,7 @@ struct bgk_solver {
     M.mabs_sums = m_sums;
     M.emitted = m_sums + 4;
     M.mabs_ff = reinterpret_cast<const float2*>(m_sums + 8);
+    M.shift = shift;
     return M;
   }
   size_t state_elems() const { return (size_t)P.nx * P.ny * P.nv; }  // (g,h) pairs
@@ -173,12 +174,16 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
     return fail(BGK_ERR_INVALID_ARG, "tile_cells must be 0, 1, 2, 4 or 8 (got %d)", c->tile_cells);
   if (c->precision != BGK_F64 && c->precision != BGK_F32 && c->precision != BGK_BF16_DEV)
     return fail(BGK_ERR_INVALID_ARG, "unknown precision %d", c->precision);
-  if (c->precision != BGK_F64) {
+  if (c->precision != BGK_F64 && c->dim == 1) {
+    // 1D reduced precision: FP32 state, one warp per cell, inflow ends
+    if (c->precision != BGK_F32) return fail(BGK_ERR_UNSUPPORTED, "dim 1 reduced precision is FP32 only");
+    if (c->nvx > 128) return fail(BGK_ERR_UNSUPPORTED, "dim 1 FP32 needs nvx <= 128 (got %d)", c->nvx);
+    if (c->bc[0].kind != BGK_BC_INFLOW || c->bc[1].kind != BGK_BC_INFLOW)
+      return fail(BGK_ERR_UNSUPPORTED, "dim 1 FP32 needs inflow boundaries");
+  } else if (c->precision != BGK_F64) {
     // the reduced-precision kernel streams 4 consecutive velocities of one
     // row per lane: rows of a multiple of 8 with c_x changing sign only on
     // multiples of 4
-    if (c->dim != 2)
-      return fail(BGK_ERR_UNSUPPORTED, "reduced precision is built for dim 2 only");
     if (c->nvx % 8 != 0)
       return fail(BGK_ERR_UNSUPPORTED, "reduced precision needs nvx a multiple of 8 (got %d)", c->nvx);
     const double dc = (c->vx_max - c->vx_min) / c->nvx;

@@ -65,6 +65,7 @@ struct MixedTables {
   const double* mabs_sums;  // [4] FP64 sums of mabs: g, c_x g, c_y g, |c|^2 g + h
   const float2* mabs_ff;    // [4] the same sums as float-float pairs
   const double* emitted;    // [kFaces] sum_{c_n>0} c_n ghost_g dv of the FP32 ghosts
+  const int* shift;         // [nv] 1D integer Courant shift (as Tables::shift)
 };
 
 // Launchers (bgk_step.cu, bgk_aux.cu, bgk_mixed.cu).  All enqueue on `stream`.

@@ -616,6 +616,145 @@ __global__ void __launch_bounds__(256, (PREC == PREC_F32 && MGL >= 6) ? 2 : 3)
   }
 }
 
+// ---- 1D, FP32 state ---------------------------------------------------------
+// One warp per cell (8 cells per CTA), no CTA barrier: the warp streams its
+// cell's velocities j = lane + 32 k (Eq. exact shift by [C], Eq. upwind on
+// the remainder r, f~ = f1 - r (f1 - f2) in flux form), sums the moments in
+// float-float, solves the cell's parameters (two linearised FP32
+// effective-parameter updates, normalisation n (pi theta)^(-1/2) in
+// float-float) and relaxes f^{n+1} = f~ + (a Phi - a f~), with
+// G = Phi_g, H = theta G (Chu, 1D).  Ends are inflow Maxwellians.
+
+// a * p0 / sqrt(pi * p3) with float-float intermediates, rounded once.
+__device__ __forceinline__ float ff_norm1d(float a, float p0, float p3) {
+  const float pi_h = 3.14159274101257324f, pi_l = -8.74227766e-08f;
+  const float xh = pi_h * p3;
+  const float xl = fmaf(pi_h, p3, -xh) + pi_l * p3;  // pi p3 = xh + xl
+  const float sh = sqrtf(xh);
+  const float sl = (fmaf(-sh, sh, xh) + xl) * (0.5f * __frcp_rn(sh));  // sqrt(pi p3) = sh + sl
+  const float nh = a * p0;
+  const float nl = fmaf(a, p0, -nh);
+  const float rd = __frcp_rn(sh);
+  const float q1 = nh * rd;
+  float r = fmaf(-q1, sh, nh);
+  r = fmaf(-q1, sl, r) + nl;
+  return fmaf(r, rd, q1);
+}
+
+template <int KV>
+__device__ __forceinline__ void mixed1d_cell(const Params& P, const MixedTables& M, const float2* __restrict__ fin,
+                                             float2* __restrict__ fout, float2* __restrict__ msum,
+                                             int* __restrict__ err, int cell) {
+  const int lane = threadIdx.x & 31;
+  const int nv = P.nvx;
+  float2 ft[KV];
+  float hs[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < KV; ++k) {
+    const int j = lane + 32 * k;
+    ft[k] = make_float2(0.f, 0.f);
+    if (j < nv) {
+      const float4 co = M.coef[j];  // (r, 0, c_x, 0)
+      const int i1 = cell - M.shift[j];
+      const int i2 = i1 - (vi_sx(M.vinfo[j]) > 0 ? 1 : -1);
+      const float2 f1 = i1 < 0 ? M.ghost[XLO * nv + j] : i1 >= P.nx ? M.ghost[XHI * nv + j]
+                                                                     : fin[(size_t)i1 * nv + j];
+      const float2 f2 = i2 < 0 ? M.ghost[XLO * nv + j] : i2 >= P.nx ? M.ghost[XHI * nv + j]
+                                                                     : fin[(size_t)i2 * nv + j];
+      ft[k].x = fmaf(-co.x, f1.x - f2.x, f1.x);
+      ft[k].y = fmaf(-co.x, f1.y - f2.y, f1.y);
+      kahan(hs[0], cs[0], ft[k].x);
+      kahan(hs[1], cs[1], co.z * ft[k].x);
+      kahan(hs[3], cs[3], fmaf(co.z * co.z, ft[k].x, ft[k].y));
+    }
+  }
+  float ls[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ls[k] = -cs[k];
+  float oh, ol;
+  warp_reduce4_ff(hs, ls, oh, ol);  // lane 8 m holds value m
+  if ((lane & 7) == 0) msum[(size_t)cell * 4 + (lane >> 3)] = make_float2(oh, ol);
+  const float sk = oh + ol;
+  const float S0 = __shfl_sync(0xffffffffu, sk, 0), S1 = __shfl_sync(0xffffffffu, sk, 8);
+  const float S3 = __shfl_sync(0xffffffffu, sk, 24);
+  const float r0 = __frcp_rn(S0);
+  float n = S0 * (float)P.dv, u = S1 * r0;
+  float th = (2.0f / 3.0f) * (S3 * r0 - u * u);
+  bool ok = n > 0.f && th > 0.f && isfinite(n) && isfinite(u) && isfinite(th);
+  if (!ok) {
+    n = 1.f;
+    u = 0.f;
+    th = 1.f;
+  }
+  const float nu = n * (P.omega == 0.5 ? sqrtf(th) : powf(th, (float)(1.0 - P.omega)));
+  const float a = P.relax_exact ? 1.0f - expf(-nu * (float)P.dt) : nu * (float)P.dt;
+  // Gaussian at (u, theta) and its central sums
+  const float inv = __frcp_rn(th);
+  float e[KV], Mm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < KV; ++k) {
+    const int j = lane + 32 * k;
+    e[k] = 0.f;
+    if (j < nv) {
+      const float d = M.cx[j] - u;
+      e[k] = expf(-(d * d) * inv);
+      float t = e[k];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        Mm[m] += t;
+        t *= d;
+      }
+    }
+  }
+  float p[3] = {n, u, th};
+  if (P.conservative) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) Mm[m] = warp_sum_f(Mm[m]);
+    const float q[3] = {n, u, th};
+    for (int it = 0; it < 2; ++it) {
+      const float w2 = (p[2] - th) * inv * inv, w1 = 2.f * (p[1] - u) * inv;
+      float S[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) S[m] = Mm[m] + w1 * Mm[m + 1] + w2 * Mm[m + 2];
+      const float rs = __frcp_rn(S[0]);
+      const float mu = S[1] * rs;
+      const float d0 = p[0] * __frsqrt_rn(3.14159265f * p[2]) * (float)P.dv * S[0];
+      const float d1 = u + mu;
+      const float d2 = (2.f / 3.f) * (S[2] * rs - mu * mu + p[2]);
+      p[0] += q[0] - d0;
+      p[1] += q[1] - d1;
+      p[2] += q[2] - d2;
+    }
+    if (!(p[0] > 0.f) || !(p[2] > 0.f) || !isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) ok = false;
+  }
+  if (!ok && lane == 0) atomicOr(err, ERR_MOMENT);
+  const float ap = ok ? ff_norm1d(a, p[0], p[2]) : 0.f;
+  const float w2 = (p[2] - th) * inv * inv, w1 = 2.f * (p[1] - u) * inv;
+  const float kappa = p[2];
+#pragma unroll
+  for (int k = 0; k < KV; ++k) {
+    const int j = lane + 32 * k;
+    if (j < nv) {
+      float2 r = ft[k];
+      if (ok) {
+        const float d = M.cx[j] - u;
+        const float ph = ap * (e[k] * fmaf(d, fmaf(d, w2, w1), 1.0f));
+        r.x += fmaf(-a, ft[k].x, ph);
+        r.y += fmaf(-a, ft[k].y, kappa * ph);
+      }
+      fout[(size_t)cell * nv + j] = r;
+    }
+  }
+}
+
+template <int KV>
+__global__ void __launch_bounds__(256) step_mixed1d_kernel(const float2* __restrict__ fin, float2* __restrict__ fout,
+                                                           float2* __restrict__ msum, const Params P,
+                                                           const MixedTables M, int* __restrict__ err) {
+  const int cell = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (cell < P.nx) mixed1d_cell<KV>(P, M, fin, fout, msum, err, cell);
+}
+
 // FP64 moments (n, ux, uy, theta) from the float-float velocity sums a step
 // published (bgk_moments, which = 1, reduced precisions).
 __global__ void msum_moments_kernel(const Params P, const MixedTables M, int prec, const float2* msum,
@@ -810,6 +949,15 @@ cudaError_t prepare_step_mixed(const Params&, int) { return cudaSuccess; }
 cudaError_t launch_step_mixed(const Params& P, int prec, const MixedTables& M, const void* fin, void* fout,
                               double4_32a* mom, int* err, cudaStream_t stream) {
   float2* msum = reinterpret_cast<float2*>(mom);  // 32 bytes per cell either way
+  if (P.dim == 1) {
+    const unsigned grid = (unsigned)((P.nx + 7) / 8);
+    const float2* fi = static_cast<const float2*>(fin);
+    float2* fo = static_cast<float2*>(fout);
+    if (P.nvx <= 32) step_mixed1d_kernel<1><<<grid, 256, 0, stream>>>(fi, fo, msum, P, M, err);
+    else if (P.nvx <= 64) step_mixed1d_kernel<2><<<grid, 256, 0, stream>>>(fi, fo, msum, P, M, err);
+    else step_mixed1d_kernel<4><<<grid, 256, 0, stream>>>(fi, fo, msum, P, M, err);
+    return cudaGetLastError();
+  }
   return prec == PREC_F32 ? dispatch_m<PREC_F32>(P, M, fin, fout, msum, err, stream)
                           : dispatch_m<PREC_BF16>(P, M, fin, fout, msum, err, stream);
 }

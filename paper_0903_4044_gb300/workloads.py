@@ -88,10 +88,11 @@ def batch_instances(seed: int = 0, cavities: int = 64, shocks: int = 16) -> list
     """Raw parameters of the batched workload: `cavities` lid-driven cavities
     with side cells from {32, 64, 96, 128, 192}, velocity grids from
     {24, 32, 40, 48}^2 on [-5, 5]^2, Kn log-uniform in [0.01, 1] and lid Mach
-    log-uniform in [0.02, 0.3], FP32 state; then `shocks` normal shocks with
+    log-uniform in [0.02, 0.3]; then `shocks` normal shocks with
     Mach uniform in [1.2, 5], cells uniform in [100, 800] on 40 mean free
     paths, and a velocity box [-V, V] with V = 4 + 3 Mach cut into
-    8 round(V / 1.2) cells (about 0.3 thermal speeds each)."""
+    8 round(V / 1.2) cells (about 0.3 thermal speeds each); every instance
+    holds an FP32 state."""
     u = (uniform_pm1(seed, 4 * cavities + 2 * shocks) + 1.0) * 0.5  # [0, 1)
     out = []
     sides, grids = (32, 64, 96, 128, 192), (24, 32, 40, 48)
@@ -109,5 +110,5 @@ def batch_instances(seed: int = 0, cavities: int = 64, shocks: int = 16) -> list
         v = 4.0 + 3.0 * mach
         out.append(dict(
             name=f"batch_shock_{k}", kind="shock", mach=mach, nx=min(800, int(100 + 701 * b)),
-            length=40.0, nvx=8 * int(round(v / 1.2)), vx=(-v, v), omega=0.5, cfl=0.5, precision="f64"))
+            length=40.0, nvx=8 * int(round(v / 1.2)), vx=(-v, v), omega=0.5, cfl=0.5, precision="f32"))
     return out

@@ -95,7 +95,9 @@ def _expect(cfg, status, text):
     (lambda c: setattr(c.bc[1], "n", 0.0), B.BGK_ERR_INVALID_ARG, "inflow needs"),
     (lambda c: setattr(c.bc[0], "uy", 0.3), B.BGK_ERR_INVALID_ARG, "uy must be 0"),
     (lambda c: setattr(c, "nvx", 5000), B.BGK_ERR_UNSUPPORTED, "exceeds"),
-    (lambda c: setattr(c, "precision", B.BGK_F32), B.BGK_ERR_UNSUPPORTED, "dim 2 only"),
+    (lambda c: setattr(c, "precision", B.BGK_BF16_DEV), B.BGK_ERR_UNSUPPORTED, "FP32 only"),
+    (lambda c: (setattr(c, "precision", B.BGK_F32), setattr(c, "nvx", 136)), B.BGK_ERR_UNSUPPORTED,
+     "nvx <= 128"),
 ])
 def test_shock_config_validation(L, mutate, status, text):
     cfg = _shock()

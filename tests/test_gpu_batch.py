@@ -24,6 +24,7 @@ MIX = [
     W.scaled(W.CAVITY_64, name="c0", n=12, nv=16, precision="f64"),
     W.scaled(W.CAVITY_64, name="c1", n=17, nv=24, precision="f32", seed=5),
     W.scaled(W.SHOCK_M2, name="s0", nx=40, precision="f64"),
+    W.scaled(W.SHOCK_M2, name="s1", nx=56, precision="f32"),
     W.scaled(W.CAVITY_64, name="c2", n=9, nv=32, precision="bf16", seed=7),
 ]
 
