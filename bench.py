@@ -383,6 +383,8 @@ def batch_arm(args, world, rank, local, pg):
     ws = W.batch_instances(0)
     b = solver.Batch(ws, stream=stream.cuda_stream, perturb=False)
     b.autotune(3)
+    if args.persistent:
+        b.set_persistent(True)
     nsteps = args.time_steps or 20
     pts = b.points()
 
@@ -418,12 +420,15 @@ def batch_arm(args, world, rank, local, pg):
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch_64_cavities_16_shocks_seed0", "instances": len(ws), "points": pts,
+                       "launch": "one persistent cooperative kernel per benchmark step (grid barrier between "
+                                 "time steps), captured in a CUDA graph" if args.persistent else
+                                 "one CUDA graph per benchmark step, one branch of step kernels per instance",
                        "time_steps": nsteps, "tiles_chosen": tiles,
                        "note": "FP32 state in every instance; "
                                "inputs larger than L2 (9.4 GB of state)"},
             "roofline": {"bound": "hbm", "note": "mixed workload; see per-kernel lines"},
             "cpu_baseline": None, "e2e": None, "clocks": clk.summary(),
-            "gpu_launches": len(ws) * nsteps * args.steps,
+            "gpu_launches": args.steps if args.persistent else len(ws) * nsteps * args.steps,
         }), flush=True)
     b.close()
 
@@ -660,6 +665,8 @@ def main():
     ap.add_argument("--precision", default="f64", choices=sorted(PRECISION),
                     help="state storage: f64, f32, or bf16 deviation from the absolute Maxwellian")
     ap.add_argument("--checkpoint-every", type=int, default=100, help="adjoint workload: steps per checkpoint")
+    ap.add_argument("--persistent", action="store_true",
+                    help="batch workload: one persistent cooperative launch per benchmark step")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
     w = workload(args.workload) if args.workload not in ("batch", "adjoint", "shock3v", "shock3v_m15") else None

@@ -222,9 +222,22 @@ BGK_API bgk_status bgk_batch_create(const bgk_config* cfgs, int count, void* cud
                                     bgk_batch** out);
 BGK_API bgk_status bgk_batch_solver(bgk_batch* b, int index, bgk_solver** out);
 BGK_API bgk_status bgk_batch_step(bgk_batch* b, int64_t nsteps);
-/* Wait for the batch stream; BGK_ERR_NUMERIC if any instance failed. */
+/* Wait for the batch stream; BGK_ERR_NUMERIC if any instance failed,
+ * BGK_ERR_TIMEOUT if a persistent launch gave up at a grid barrier. */
 BGK_API bgk_status bgk_batch_sync(bgk_batch* b);
 BGK_API bgk_status bgk_batch_destroy(bgk_batch* b);
+
+/* Persistent mode (enable = 1): each bgk_batch_step call becomes one
+ * cooperative launch, captured in a CUDA graph, in which every CTA of a
+ * resident grid walks the work units (blocks of cells of every instance)
+ * of one step, then waits at a grid barrier before the next step.  FP32
+ * instances only (2D and 1D); a 2D instance whose tile needs more than 16
+ * velocities per lane gets a smaller tile.  A barrier wait longer than
+ * timeout_s seconds records a timeout and ends the launch, leaving the
+ * steps incomplete: bgk_batch_sync then returns BGK_ERR_TIMEOUT (and clears
+ * the record).  enable = 0 returns to one graph branch per instance.
+ * Results equal those of the instances stepped alone with the same tiles. */
+BGK_API bgk_status bgk_batch_set_persistent(bgk_batch* b, int enable, double timeout_s);
 
 /* Autotuner: time trial_steps steps for every admissible tile_cells value
  * (cells per CTA: 1, 2, 4, 8) on the solver's own state, which is saved

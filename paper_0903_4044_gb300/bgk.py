@@ -30,7 +30,7 @@ EXPORTS = (
     "bgk_step_noalloc", "bgk_batch_create", "bgk_batch_solver", "bgk_batch_step", "bgk_batch_sync",
     "bgk_batch_destroy", "bgk_autotune", "bgk_batch_autotune", "bgk_adjoint_lid_shear",
     "bgk3v_create", "bgk3v_destroy", "bgk3v_get_info", "bgk3v_init_step", "bgk3v_set_state",
-    "bgk3v_get_state", "bgk3v_step", "bgk3v_moments", "bgk3v_sync",
+    "bgk3v_get_state", "bgk3v_step", "bgk3v_moments", "bgk3v_sync", "bgk_batch_set_persistent",
 )
 
 
@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
             "bgk3v_step": ([_P, ctypes.c_int64], ctypes.c_int),
             "bgk3v_moments": ([_P, ctypes.c_int, _P, ctypes.c_int], ctypes.c_int),
             "bgk3v_sync": ([_P], ctypes.c_int),
+            "bgk_batch_set_persistent": ([_P, ctypes.c_int, ctypes.c_double], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -365,3 +366,7 @@ def bgk3v_moments(h: int, out, which: int = 0) -> None:
 
 def bgk3v_sync(h: int) -> None:
     _check(lib().bgk3v_sync(h), "bgk3v_sync")
+
+
+def bgk_batch_set_persistent(b: int, enable: bool = True, timeout_s: float = 5.0) -> None:
+    _check(lib().bgk_batch_set_persistent(b, int(enable), timeout_s), "bgk_batch_set_persistent")

@@ -899,6 +899,17 @@ struct bgk_batch {
     cudaGraphExec_t exec = nullptr;
   };
   std::vector<Graph> graphs;
+  // persistent mode: one cooperative kernel per bgk_batch_step call
+  int persistent = 0;
+  double timeout_s = 5.0;
+  bgk::GridBarrier* bar = nullptr;
+  int* gerr = nullptr;
+  struct PGraph {
+    std::vector<int64_t> key;  // per instance: parity and generation; then steps
+    cudaGraphExec_t exec = nullptr;
+    bgk::PInstance* d_inst = nullptr;
+  };
+  std::vector<PGraph> pgraphs;
 };
 
 namespace {
@@ -907,6 +918,12 @@ void batch_release(bgk_batch* b) {
   if (!b) return;
   for (auto& g : b->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& g : b->pgraphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.d_inst) cudaFree(g.d_inst);
+  }
+  if (b->bar) cudaFree(b->bar);
+  if (b->gerr) cudaFree(b->gerr);
   for (auto* s : b->inst) release(s);
   for (auto st : b->branch)
     if (st) cudaStreamDestroy(st);
@@ -971,9 +988,141 @@ bgk_status batch_graph(bgk_batch* b, int steps, cudaGraphExec_t* out) {
   return BGK_OK;
 }
 
+// The captured persistent launch for `steps` steps from the instances'
+// current buffers: a reset of the grid barrier, then the cooperative kernel.
+bgk_status batch_pgraph(bgk_batch* b, int steps, cudaGraphExec_t* out) {
+  std::vector<int64_t> key;
+  for (auto* s : b->inst) {
+    key.push_back(s->cur);
+    key.push_back(s->gen);
+  }
+  key.push_back(steps);
+  for (auto& g : b->pgraphs)
+    if (g.key == key) {
+      *out = g.exec;
+      return BGK_OK;
+    }
+  std::vector<bgk::PInstance> h(b->inst.size());
+  int units = 0;
+  size_t smem = 0;
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    bgk_solver* s = b->inst[i];
+    bgk::PInstance& I = h[i];
+    std::memset(&I, 0, sizeof(I));
+    I.P = s->P;
+    I.M = s->mtables();
+    I.f_even = s->f[s->cur];
+    I.f_odd = s->f[s->cur ^ 1];
+    I.msum = reinterpret_cast<float2*>(s->mom_step);
+    I.err = s->err;
+    I.kind = bgk::persistent_kind(s->P);
+    I.unit0 = units;
+    I.units = bgk::persistent_units(s->P, I.kind);
+    units += I.units;
+    smem = std::max(smem, bgk::persistent_smem(s->P));
+  }
+  int grid = 0;
+  cudaError_t e = bgk::persistent_grid(smem, &grid);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent occupancy");
+  if (grid < 1) return fail(BGK_ERR_UNSUPPORTED, "the persistent kernel does not fit on an SM");
+  grid = std::min(grid, units);
+  bgk::PInstance* d_inst = nullptr;
+  e = cudaMalloc(&d_inst, sizeof(bgk::PInstance) * h.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(d_inst, h.data(), sizeof(bgk::PInstance) * h.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (d_inst) cudaFree(d_inst);
+    return cuda_fail(e, "persistent descriptors");
+  }
+  const long long spins = (long long)std::max(1.0, std::min(9.0e18, b->timeout_s / 2.0e-7));
+  cudaGraph_t graph = nullptr;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+  cudaError_t le = e;
+  if (le == cudaSuccess) le = cudaMemsetAsync(b->bar, 0, sizeof(bgk::GridBarrier), b->origin);
+  if (le == cudaSuccess) le = bgk::upload_persistent(d_inst, (int)h.size(), b->origin);
+  if (le == cudaSuccess)
+    le = bgk::launch_persistent((int)h.size(), units, steps, b->bar, b->gerr, spins, grid, smem, b->origin);
+  if (e == cudaSuccess) e = cudaStreamEndCapture(b->origin, &graph);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaFree(d_inst);
+    return cuda_fail(le != cudaSuccess ? le : e, "persistent batch capture");
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaFree(d_inst);
+    return cuda_fail(e, "persistent graph instantiate");
+  }
+  if (b->pgraphs.size() >= 4) {
+    cudaGraphExecDestroy(b->pgraphs.front().exec);
+    cudaFree(b->pgraphs.front().d_inst);
+    b->pgraphs.erase(b->pgraphs.begin());
+  }
+  b->pgraphs.push_back({key, exec, d_inst});
+  *out = exec;
+  return BGK_OK;
+}
+
+void drop_pgraphs(bgk_batch* b) {
+  for (auto& g : b->pgraphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.d_inst) cudaFree(g.d_inst);
+  }
+  b->pgraphs.clear();
+}
+
 }  // namespace
 
 extern "C" {
+
+bgk_status bgk_batch_set_persistent(bgk_batch* b, int enable, double timeout_s) {
+  BGK_GUARD_BEGIN
+  if (!b) return fail(BGK_ERR_INVALID_ARG, "null batch");
+  if (enable != 0 && enable != 1) return fail(BGK_ERR_INVALID_ARG, "enable must be 0 or 1");
+  if (!(timeout_s > 0.0) || !std::isfinite(timeout_s)) return fail(BGK_ERR_INVALID_ARG, "timeout must be > 0");
+  bgk_status st = select_device(b->inst[0]);
+  if (st != BGK_OK) return st;
+  if (enable) {
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+      bgk_solver* s = b->inst[i];
+      if (s->prec != bgk::PREC_F32)
+        return fail(BGK_ERR_UNSUPPORTED, "instance %zu: the persistent kernel runs FP32 instances only", i);
+      if (b->inst.size() > (size_t)bgk::kMaxPersistInstances)
+        return fail(BGK_ERR_UNSUPPORTED, "the persistent kernel takes at most %d instances", bgk::kMaxPersistInstances);
+      if (bgk::persistent_kind(s->P) < 0) {
+        // 2D: the largest admissible tile with at most 4 groups per lane
+        int chosen = 0;
+        for (int t : {8, 4, 2, 1}) {
+          if (!tile_admissible(s, t)) continue;
+          bgk::Params q = s->P;
+          q.tile = t;
+          if (bgk::persistent_kind(q) >= 0) {
+            chosen = t;
+            break;
+          }
+        }
+        if (!chosen) return fail(BGK_ERR_UNSUPPORTED, "instance %zu: no tile the persistent kernel supports", i);
+        cudaError_t e = set_tile(s, chosen);
+        if (e != cudaSuccess) return cuda_fail(e, "persistent tile");
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    if (!b->bar) e = cudaMalloc(&b->bar, sizeof(bgk::GridBarrier));
+    if (e == cudaSuccess && !b->gerr) {
+      e = cudaMalloc(&b->gerr, sizeof(int));
+      if (e == cudaSuccess) e = cudaMemset(b->gerr, 0, sizeof(int));
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "persistent barrier");
+  }
+  drop_pgraphs(b);
+  b->persistent = enable;
+  b->timeout_s = timeout_s;
+  return BGK_OK;
+  BGK_GUARD_END
+}
 
 bgk_status bgk_autotune(bgk_solver* s, int trial_steps, int* tile_out) {
   BGK_GUARD_BEGIN
@@ -1087,6 +1236,19 @@ bgk_status bgk_batch_step(bgk_batch* b, int64_t nsteps) {
   if (nsteps == 0) return BGK_OK;
   bgk_status st = select_device(b->inst[0]);
   if (st != BGK_OK) return st;
+  if (b->persistent) {
+    const int k = (int)std::min<int64_t>(nsteps, 1 << 30);
+    cudaGraphExec_t exec = nullptr;
+    st = batch_pgraph(b, k, &exec);
+    if (st != BGK_OK) return st;
+    cudaError_t e = cudaGraphLaunch(exec, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent batch launch");
+    for (auto* s : b->inst) {
+      s->steps_done += k;
+      if (k & 1) s->cur ^= 1;
+    }
+    nsteps -= k;
+  }
   while (nsteps > 0) {
     const int k = (int)std::min<int64_t>(nsteps, kChunk);
     cudaGraphExec_t exec = nullptr;
@@ -1107,6 +1269,17 @@ bgk_status bgk_batch_step(bgk_batch* b, int64_t nsteps) {
 bgk_status bgk_batch_sync(bgk_batch* b) {
   BGK_GUARD_BEGIN
   if (!b) return fail(BGK_ERR_INVALID_ARG, "null batch");
+  if (b->gerr) {
+    int h = 0;
+    cudaError_t e = cudaSetDevice(b->inst[0]->device);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, b->gerr, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess && h) e = cudaMemsetAsync(b->gerr, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch synchronize");
+    if (h & bgk::ERR_TIMEOUT)
+      return fail(BGK_ERR_TIMEOUT, "a grid barrier of the persistent batch kernel timed out; the steps did not complete");
+  }
   for (size_t i = 0; i < b->inst.size(); ++i) {
     bgk_status st = bgk_sync(b->inst[i]);
     if (st != BGK_OK) {

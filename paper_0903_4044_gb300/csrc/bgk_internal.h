@@ -14,7 +14,7 @@ enum { BC_INFLOW = 0, BC_DIFFUSE = 1, BC_SPECULAR = 2 };
 enum { PREC_F64 = 0, PREC_F32 = 1, PREC_BF16 = 2 };  // as bgk_precision
 
 // Error bits written by kernels into the solver's device flag.
-enum { ERR_MOMENT = 1, ERR_EFFECTIVE = 2 };
+enum { ERR_MOMENT = 1, ERR_EFFECTIVE = 2, ERR_TIMEOUT = 4 };
 
 // Effective-parameter iteration (Sec. 2.1, remark on exact conservation):
 // p <- p + (q - D(p)) until an update is below kEffTol, at most kEffMaxIt
@@ -91,6 +91,39 @@ cudaError_t launch_build_mixed_tables(const Params& P, const Tables& T, const Mi
                                       cudaStream_t stream);
 size_t step_mixed_smem_bytes(const Params& P, int tile, int prec);
 int mixed_groups_per_lane(const Params& P, int tile);
+// Persistent batch (bgk_mixed.cu): one kernel advances many FP32
+// instances by several steps, a grid barrier between steps.
+enum {
+  PK_2D_G1_M2 = 0, PK_2D_G1_M4, PK_2D_G2_M2, PK_2D_G2_M4, PK_2D_G4_M2, PK_2D_G4_M4, PK_2D_G8_M2,
+  PK_1D_K1, PK_1D_K2, PK_1D_K4, PK_KINDS
+};
+struct PInstance {
+  Params P;
+  MixedTables M;
+  const void* f_even;  // input of even steps (output of odd steps)
+  void* f_odd;         // output of even steps
+  float2* msum;
+  int* err;
+  int kind;            // PK_*
+  int unit0, units;    // first work unit, work units per step
+  int pad;
+};
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+// Kind of an FP32 instance for the persistent kernel (-1: not supported).
+int persistent_kind(const Params& P);
+int persistent_units(const Params& P, int kind);
+size_t persistent_smem(const Params& P);
+// Resident CTAs of the persistent kernel for dynamic shared memory smem.
+cudaError_t persistent_grid(size_t smem, int* grid);
+constexpr int kMaxPersistInstances = 160;
+// Copy ninst descriptors (device memory) to the kernel's constant array.
+cudaError_t upload_persistent(const PInstance* d_inst, int ninst, cudaStream_t stream);
+cudaError_t launch_persistent(int ninst, int total_units, int nsteps, GridBarrier* bar, int* gerr,
+                              long long spin_limit, int grid, size_t smem, cudaStream_t stream);
+
 // Full 3D velocity grid, one spatial dimension (bgk_step3v.cu).
 struct Params3v {
   int nx, nvx, nvy, nvz, nv;

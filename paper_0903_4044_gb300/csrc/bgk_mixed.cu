@@ -483,24 +483,30 @@ __device__ __forceinline__ void store_result(void* fout, size_t idx, const float
 
 }  // namespace
 
-// 768 resident threads per SM at most 80 registers each; FP32 with 6 groups
-// per lane gets 128 registers and 2 CTAs per SM instead (measured faster than
-// spilling; BF16 keeps 3 CTAs and spills a little, also measured).
+// Shared scratch of one block of G cells (WPC = 8/G warps per cell).
+template <int G>
+struct MixedShared {
+  float2 part[G][8 / G][4];  // float-float partial moment sums per warp
+  float gp[G][8 / G][10];    // central sums of the Gaussian factors per warp
+  CellPar cp[G];             // per-cell parameters
+};
+
+// One block of G cells of a 2D reduced-precision step (all 256 threads of
+// the CTA; phx holds G (nvx + nvy) floats).  Used by the per-instance kernel
+// below and by the persistent batch kernel.
 template <int PREC, int G, int MGL>
-__global__ void __launch_bounds__(256, (PREC == PREC_F32 && MGL >= 6) ? 2 : 3)
-    step_mixed_kernel(const void* __restrict__ fin, void* __restrict__ fout, float2* __restrict__ msum,
-                      const Params P, const MixedTables M, int* __restrict__ err) {
+__device__ __forceinline__ void mixed2d_block(const Params& P, const MixedTables& M, const void* __restrict__ fin,
+                                              void* __restrict__ fout, float2* __restrict__ msum,
+                                              int* __restrict__ err, int blk, float* phx, MixedShared<G>& S) {
   constexpr int WPC = 8 / G;
-  extern __shared__ float4 smemf4[];
-  float* phx = reinterpret_cast<float*>(smemf4);
   float* phy = phx + G * P.nvx;
-  __shared__ float2 s_part[G][WPC][4];
-  __shared__ float s_gp[G][WPC][10];
-  __shared__ CellPar s_cp[G];
+  auto& s_part = S.part;
+  auto& s_gp = S.gp;
+  auto& s_cp = S.cp;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = warp / WPC, wc = warp % WPC;
-  const int cell = blockIdx.x * G + c;
+  const int cell = blk * G + c;
   const bool live = cell < P.nx * P.ny;
   const int ngroups = P.nv >> 2;
   const int lic = wc * 32 + lane;
@@ -614,6 +620,18 @@ __global__ void __launch_bounds__(256, (PREC == PREC_F32 && MGL >= 6) ? 2 : 3)
       store_result<PREC>(fout, C.c0 + j0, r);
     }
   }
+}
+
+// 768 resident threads per SM at most 80 registers each; FP32 with 6 groups
+// per lane gets 128 registers and 2 CTAs per SM instead (measured faster than
+// spilling; BF16 keeps 3 CTAs and spills a little, also measured).
+template <int PREC, int G, int MGL>
+__global__ void __launch_bounds__(256, (PREC == PREC_F32 && MGL >= 6) ? 2 : 3)
+    step_mixed_kernel(const void* __restrict__ fin, void* __restrict__ fout, float2* __restrict__ msum,
+                      const Params P, const MixedTables M, int* __restrict__ err) {
+  extern __shared__ float4 smemf4[];
+  __shared__ MixedShared<G> S;
+  mixed2d_block<PREC, G, MGL>(P, M, fin, fout, msum, err, blockIdx.x, reinterpret_cast<float*>(smemf4), S);
 }
 
 // ---- 1D, FP32 state ---------------------------------------------------------
@@ -753,6 +771,162 @@ __global__ void __launch_bounds__(256) step_mixed1d_kernel(const float2* __restr
                                                            const MixedTables M, int* __restrict__ err) {
   const int cell = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (cell < P.nx) mixed1d_cell<KV>(P, M, fin, fout, msum, err, cell);
+}
+
+// ---- persistent batch ----------------------------------------------------------
+// One cooperative launch advances every instance of a batch (FP32, 2D and
+// 1D) by nsteps.  Work units are blocks of cells (G cells of a 2D instance,
+// 8 cells of a 1D one), numbered instance after instance; CTA b takes the
+// units b, b + gridDim.x, ... (so that at any moment the grid works on a
+// window of neighbouring units, whose upwind sources are then on chip); the
+// instance descriptors sit in constant memory.  Between steps a grid
+// barrier: each CTA announces
+// its arrival and waits for the generation count to move, for at most
+// spin_limit polls, after which it records ERR_TIMEOUT and returns (every
+// other CTA then gives up at its own limit), so the launch always ends.
+
+__device__ __forceinline__ void mixed1d_unit(const PInstance& I, const void* fin, void* fout, int blk) {
+  const int cell = blk * 8 + (threadIdx.x >> 5);
+  if (cell >= I.P.nx) return;
+  const float2* fi = static_cast<const float2*>(fin);
+  float2* fo = static_cast<float2*>(fout);
+  switch (I.kind) {
+    case PK_1D_K1: mixed1d_cell<1>(I.P, I.M, fi, fo, I.msum, I.err, cell); break;
+    case PK_1D_K2: mixed1d_cell<2>(I.P, I.M, fi, fo, I.msum, I.err, cell); break;
+    default: mixed1d_cell<4>(I.P, I.M, fi, fo, I.msum, I.err, cell); break;
+  }
+}
+
+// One work unit of each kind, compiled apart (called, not inlined: measured
+// fastest of the inlined / called and 2 / 3 CTAs-per-SM variants).
+#define kPersistInline __noinline__
+constexpr int kPersistMinBlocks = 3;
+template <int G, int MGL>
+__device__ kPersistInline void unit2d(const PInstance& I, const void* fin, void* fout, int blk, float* phx, char* raw) {
+  mixed2d_block<PREC_F32, G, MGL>(I.P, I.M, fin, fout, I.msum, I.err, blk, phx,
+                                  *reinterpret_cast<MixedShared<G>*>(raw));
+}
+__device__ kPersistInline void unit1d(const PInstance& I, const void* fin, void* fout, int blk) {
+  mixed1d_unit(I, fin, fout, blk);
+}
+
+// Returns false when the wait ran out (or another CTA already failed).
+__device__ bool grid_barrier(GridBarrier* bar, int* gerr, long long spin_limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = &bar->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    if (atomicAdd(&bar->count, 1u) + 1u == gridDim.x) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (++spins > spin_limit || *(volatile int*)gerr) {
+          atomicOr(gerr, ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Instance descriptors of the launch, copied in by the graph before the
+// kernel (read-only memory: the step's shared-memory stores cannot alias it).
+__constant__ PInstance c_pinst[kMaxPersistInstances];
+
+__global__ void __launch_bounds__(256, kPersistMinBlocks)
+    batch_persistent_kernel(int ninst, int total_units, int nsteps, GridBarrier* bar, int* gerr,
+                            long long spin_limit) {
+  extern __shared__ float4 dynf4[];
+  float* phx = reinterpret_cast<float*>(dynf4);
+  __shared__ __align__(16) char s_raw[sizeof(MixedShared<8>) > sizeof(MixedShared<1>) ? sizeof(MixedShared<8>)
+                                                                                       : sizeof(MixedShared<1>)];
+  for (int step = 0; step < nsteps; ++step) {
+    const bool even = (step & 1) == 0;
+    int i = 0;
+    for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+      while (c_pinst[i].unit0 + c_pinst[i].units <= u) ++i;  // u grows: scan forward
+      const PInstance& I = c_pinst[i];
+      const void* fin = even ? I.f_even : I.f_odd;
+      void* fout = even ? I.f_odd : const_cast<void*>(I.f_even);
+      const int blk = u - I.unit0;
+      switch (I.kind) {
+        case PK_2D_G1_M2: unit2d<1, 2>(I, fin, fout, blk, phx, s_raw); break;
+        case PK_2D_G1_M4: unit2d<1, 4>(I, fin, fout, blk, phx, s_raw); break;
+        case PK_2D_G2_M2: unit2d<2, 2>(I, fin, fout, blk, phx, s_raw); break;
+        case PK_2D_G2_M4: unit2d<2, 4>(I, fin, fout, blk, phx, s_raw); break;
+        case PK_2D_G4_M2: unit2d<4, 2>(I, fin, fout, blk, phx, s_raw); break;
+        case PK_2D_G4_M4: unit2d<4, 4>(I, fin, fout, blk, phx, s_raw); break;
+        case PK_2D_G8_M2: unit2d<8, 2>(I, fin, fout, blk, phx, s_raw); break;
+        default: unit1d(I, fin, fout, blk); break;
+      }
+    }
+    if (!grid_barrier(bar, gerr, spin_limit)) return;
+  }
+}
+
+cudaError_t upload_persistent(const PInstance* d_inst, int ninst, cudaStream_t stream) {
+  if (ninst > kMaxPersistInstances) return cudaErrorInvalidValue;
+  return cudaMemcpyToSymbolAsync(c_pinst, d_inst, sizeof(PInstance) * (size_t)ninst, 0, cudaMemcpyDeviceToDevice,
+                                 stream);
+}
+
+int persistent_kind(const Params& P) {
+  if (P.dim == 1) {
+    if (P.nvx > 128) return -1;
+    return P.nvx <= 32 ? PK_1D_K1 : P.nvx <= 64 ? PK_1D_K2 : PK_1D_K4;
+  }
+  const int m = mixed_groups_per_lane(P, P.tile);
+  switch (P.tile) {
+    case 1: return m == 2 ? PK_2D_G1_M2 : m == 4 ? PK_2D_G1_M4 : -1;
+    case 2: return m == 2 ? PK_2D_G2_M2 : m == 4 ? PK_2D_G2_M4 : -1;
+    case 4: return m == 2 ? PK_2D_G4_M2 : m == 4 ? PK_2D_G4_M4 : -1;
+    case 8: return m == 2 ? PK_2D_G8_M2 : -1;
+  }
+  return -1;
+}
+
+int persistent_units(const Params& P, int kind) {
+  if (kind >= PK_1D_K1) return (P.nx + 7) / 8;
+  return (P.nx * P.ny + P.tile - 1) / P.tile;
+}
+
+size_t persistent_smem(const Params& P) { return P.dim == 1 ? 0 : mixed_factor_bytes(P, P.tile); }
+
+cudaError_t persistent_grid(size_t smem, int* grid) {
+  int dev = 0, per_sm = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel, 256, smem);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *grid = per_sm * sms;
+  return e;
+}
+
+cudaError_t launch_persistent(int ninst, int total_units, int nsteps, GridBarrier* bar, int* gerr,
+                              long long spin_limit, int grid, size_t smem, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident: the grid barrier needs it
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_persistent_kernel, ninst, total_units, nsteps, bar, gerr, spin_limit);
 }
 
 // FP64 moments (n, ux, uy, theta) from the float-float velocity sums a step

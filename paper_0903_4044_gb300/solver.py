@@ -182,6 +182,14 @@ class Batch:
         for s in self.solvers:
             s.info = B.bgk_get_info(s.h)
 
+    def set_persistent(self, enable: bool = True, timeout_s: float = 5.0) -> None:
+        """One cooperative launch per step() call (FP32 instances only)."""
+        B.bgk_batch_set_persistent(self.h, enable, timeout_s)
+        for s in self.solvers:
+            s.info = B.bgk_get_info(s.h)
+        for s in self.solvers:
+            s.info = B.bgk_get_info(s.h)
+
     def points(self) -> int:
         return sum(s.ncell * s.nv for s in self.solvers)
 

@@ -95,3 +95,55 @@ def test_batch_autotune_then_step():
     st = b.solvers[0].get_state()
     assert np.abs(st[..., 0] - g1).max() / np.abs(g1).max() < 1e-12
     b.close()
+
+
+# ---------------------------------------------------------------------------
+# persistent mode: one cooperative launch per step() call
+# ---------------------------------------------------------------------------
+MIX32 = [
+    W.scaled(W.CAVITY_64, name="p0", n=13, nv=48, precision="f32", seed=2),
+    W.scaled(W.CAVITY_64, name="p1", n=21, nv=32, precision="f32", seed=3),
+    W.scaled(W.SHOCK_M2, name="p2", nx=57, precision="f32"),
+    W.scaled(W.CAVITY_64, name="p3", n=8, nv=24, precision="f32", seed=4),
+    dict(W.SHOCK_M2, name="p4", mach=5.0, nx=90, nvx=128, vx=(-19.0, 19.0), precision="f32"),
+    dict(W.SHOCK_M2, name="p5", mach=1.2, nx=33, nvx=48, vx=(-7.6, 7.6), precision="f32"),
+]
+
+
+def test_persistent_equals_independent_solvers():
+    b = solver.Batch(MIX32)
+    b.set_persistent(True)
+    tiles = [int(s.info.tile_cells) for s in b.solvers]
+    b.step(37)
+    b.step(4)
+    b.sync()
+    for w, sb, t in zip(MIX32, b.solvers, tiles):
+        s = _single(dict(w, tile_cells=t))
+        s.step(41)
+        assert np.array_equal(sb.get_state(), s.get_state()), w["name"]
+        assert np.array_equal(sb.moments(which=1), s.moments(which=1)), w["name"]
+        s.close()
+    b.close()
+
+
+def test_persistent_needs_fp32():
+    b = solver.Batch(MIX[:2])
+    with pytest.raises(B.BgkError) as e:
+        b.set_persistent(True)
+    assert e.value.status == B.BGK_ERR_UNSUPPORTED
+    b.close()
+
+
+def test_persistent_barrier_timeout_is_reported():
+    # a wait limit far below one step's duration: the grid barrier gives up,
+    # the launch ends, sync reports the timeout and the batch stays usable
+    b = solver.Batch(MIX32[:3])
+    b.set_persistent(True, timeout_s=1e-7)
+    b.step(3)
+    with pytest.raises(B.BgkError) as e:
+        b.sync()
+    assert e.value.status == B.BGK_ERR_TIMEOUT
+    b.set_persistent(True, timeout_s=5.0)
+    b.step(2)
+    b.sync()
+    b.close()
