@@ -284,11 +284,13 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
   return BGK_OK;
 }
 
-// Largest tile (cells per CTA) that keeps two CTAs' staged state within an
-// SM's shared memory and still gives every SM at least two CTAs.
+// Largest tile (cells per CTA) that keeps two CTAs' shared memory within an
+// SM and still gives every SM at least two CTAs; FP64 stops at 4 cells per
+// CTA (measured best on 64^2 x 32^2 and 256^2 x 48^2 cavities).
 int auto_tile(const bgk::Params& P, int prec, int sms) {
   const long long ncell = (long long)P.nx * P.ny;
   for (int t : {8, 4, 2}) {
+    if (prec == BGK_F64 && t > 4) continue;
     // reduced precisions: at most 24 velocities per lane (instantiated)
     if (prec != BGK_F64 && bgk::mixed_groups_per_lane(P, t) == 0) continue;
     if (step_smem(P, prec, t) <= kAutoSmem && (ncell + t - 1) / t >= 2LL * sms) return t;
