@@ -44,6 +44,31 @@ DETAIL = {"f64": "FP64 state and arithmetic",
           "bf16": "BF16 deviation from the absolute Maxwellian; FP32 arithmetic; float-float moment sums finished in FP64; FP64 per-cell parameters"}
 
 
+# DRAM bytes per launch of the step kernel from an ncu capture (dram__bytes_
+# read.sum + write.sum), valid only for the kernel sources that were
+# captured: the SHA-1 of those files must match, else traffic is reported as
+# null.  Captures and commands: profiles/step_f64_cavity64.md.
+MEASURED_TRAFFIC = {
+    ("cavity_kn0.1_ma0.1_64x64_v32x32_f64", "f64"): {
+        "bytes": 96.1e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
+        "sha1": "68a8f65c6613bba3708b61647bb9fa3bd331a438"},
+}
+
+
+def measured_traffic(workload: str, precision: str):
+    """Captured DRAM bytes per launch for this workload, if the captured kernel is the one built."""
+    import hashlib
+
+    rec = MEASURED_TRAFFIC.get((workload, precision))
+    if rec is None:
+        return None
+    h = hashlib.sha1()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, "paper_0903_4044_gb300", f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest() == rec["sha1"] else None
+
+
 def load_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -298,7 +323,8 @@ def ours_arm(args, w, world, rank, local, pg):
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peaks["source"]}
     kname = "bgk::step_f64_kernel" if args.precision == "f64" else "bgk::step_mixed_kernel"
-    roof.update({"traffic": args.traffic, "kernel": kname,
+    traffic = args.traffic if args.traffic is not None else measured_traffic(w["name"], args.precision)
+    roof.update({"traffic": traffic, "kernel": kname,
                  "launch_ms": per_launch * 1e3, "hbm_gbs": hbm_achieved,
                  "hbm_frac": hbm_achieved / peaks["hbm_gbs"], "fp64_tflops": alu_achieved})
 
