@@ -256,9 +256,8 @@ __global__ void __launch_bounds__(32 * G, 2) adj_step_kernel(const Params P, con
   extern __shared__ double sh[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ncell = P.nx * P.ny, nvxy = P.nvx + P.nvy;
-  double2* sl = reinterpret_cast<double2*>(sh) + (size_t)warp * P.nv;  // lambda^{n+1} of this warp's cell
-  double* ex = sh + 2 * (size_t)G * P.nv + (size_t)warp * nvxy;      // n/(pi theta) e^{-(c_x-u_x)^2/theta}
-  double* ey = ex + P.nvx;                                            // e^{-(c_y-u_y)^2/theta}
+  double* ex = sh + (size_t)warp * nvxy;  // n/(pi theta) e^{-(c_x-u_x)^2/theta}
+  double* ey = ex + P.nvx;                // e^{-(c_y-u_y)^2/theta}
   __shared__ double s_sum[G][8], s_cf[G][5];
   const int cell = blockIdx.x * G + warp;
   const bool live = cell < ncell;
@@ -266,9 +265,12 @@ __global__ void __launch_bounds__(32 * G, 2) adj_step_kernel(const Params P, con
   const size_t base = (size_t)cell * P.nv;
   const int dmask = live ? diffuse_faces(P, ix, iy) : 0;
 
-  // 1. lambda^{n+1} at this cell
+  // 1. lambda^{n+1} at this cell, parked in the cell's output slots (each
+  // lane rereads only what it wrote; shared-memory staging, 16 B per
+  // velocity, held an SM to 3 CTAs)
+  double2* sl = out + base;
   if (live) {
-    double2* dst = collide ? sl : out + base;
+    double2* dst = sl;
     if (tilde) {
       stream_adjoint(P, T, cell, ix, iy, dmask, fn1, lam_in, dghost, demit, duw, dst);
     } else {
@@ -407,7 +409,7 @@ cudaError_t launch_adj_seed(const Params& P, const Tables& T, const double2* f, 
 
 namespace {
 
-size_t adj_cell_bytes(const Params& P) { return sizeof(double) * (2 * (size_t)P.nv + P.nvx + P.nvy); }
+size_t adj_cell_bytes(const Params& P) { return sizeof(double) * (size_t)(P.nvx + P.nvy); }
 
 template <int G>
 cudaError_t launch_adj_g(const Params& P, const Tables& T, const double2* fn1,
@@ -428,8 +430,8 @@ cudaError_t launch_adj_g(const Params& P, const Tables& T, const double2* fn1,
 
 }  // namespace
 
-// Cells per CTA: 4 while four cells' lambda and Gaussian factors fit in
-// 100 KB (two CTAs per SM), else 2, else 1.
+// Cells per CTA: 4 while four cells' Gaussian factors fit in 100 KB (two
+// CTAs per SM), else 2, else 1.
 cudaError_t launch_adj_step(const Params& P, const Tables& T, const double2* fn1,
                             const double4_32a* qn, const double4_32a* pn, const double2* lam_in, int tilde,
                             int collide, double2* out, const double2* dghost, double demit, double* dlnl,
