@@ -1331,7 +1331,7 @@ bgk_status bgk_batch_autotune(bgk_batch* b, int trial_steps) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Adjoint driver (kernels in bgk_adjoint.cu).
+// Adjoint host loop (kernels in bgk_adjoint.cu).
 //   forward:   f^0 .. f^N, saving f^{mK} (M checkpoints);
 //   seed:      lambda^N = dJ/df^N, J per lid cell, explicit dJ/dU_W;
 //   reverse:   per segment m = M-1 .. 0, recompute f^{mK} .. f^{mK+len}
