@@ -330,7 +330,7 @@ def ours_arm(args, w, world, rank, local, pg):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = max(1, int(1.0e9 // (ncell * nv)))
+        sample = max(1, int(3.0e9 // (ncell * nv)))  # about 10 s on 16 host cores
         rate, dt, threads = oracle_sample(w, sample)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{sample} time steps of {w['name']} ({dt:.1f} s)"}
