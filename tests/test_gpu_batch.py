@@ -147,3 +147,27 @@ def test_persistent_barrier_timeout_is_reported():
     b.step(2)
     b.sync()
     b.close()
+
+
+# ---------------------------------------------------------------------------
+# the batched workload at full size (64 cavities + 16 shocks, FP32)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("persistent", [False, True])
+def test_full_batch_sampled_instances(persistent):
+    # the launch configuration the benchmark times: tiles from the autotuner,
+    # then steps of the whole batch (graph branches or the persistent
+    # kernel); sampled instances bit for bit as when stepped alone
+    ws = W.batch_instances(0)
+    b = solver.Batch(ws)
+    b.autotune(2)
+    if persistent:
+        b.set_persistent(True)
+    tiles = [int(s.info.tile_cells) for s in b.solvers]
+    b.step(5)
+    b.sync()
+    for i in (0, 17, 40, 63, 64, 71, 79):
+        s = _single(dict(ws[i], tile_cells=tiles[i]))
+        s.step(5)
+        assert np.array_equal(b.solvers[i].get_state(), s.get_state()), ws[i]["name"]
+        s.close()
+    b.close()

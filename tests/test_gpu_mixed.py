@@ -205,3 +205,16 @@ def test_shock_reduced_precision_restrictions():
     with pytest.raises(B.BgkError) as e:
         solver.Solver(cfg)
     assert e.value.status == B.BGK_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("name", ["f32", "bf16"])
+def test_full_size_one_step(name):
+    # the 256x256 x 48x48 cavity the benchmark times (automatic tile), one
+    # step from the perturbed rest state, the whole state against the oracle
+    s, prob, g, h = _pair(W.CAVITY_256, PRECS[name])
+    s.step(1)
+    g1, h1, _ = oracle.step(prob, g, h, 1)
+    st = np.empty((s.ncell, s.nv, 2))
+    B.bgk_get_state(s.h, st)
+    _check_state(name, st, prob, g1, h1)
+    s.close()
