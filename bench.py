@@ -200,27 +200,85 @@ def oracle_sample(w: dict, sample_steps: int):
     return prob.ncell * prob.nv * sample_steps / dt, dt, oracle.threads()
 
 
+def reference_sampler(name: str, w: dict | None):
+    """(label, updates per sample, sample function) for the oracle on a bounded
+    sample of workload `name`; the function returns (seconds, threads)."""
+    import oracle
+    from paper_0903_4044_gb300 import workloads as W
+
+    oracle.build()
+    if name in ("shock3v", "shock3v_m15"):
+        w3 = W.SHOCK3V_M3 if name == "shock3v" else W.SHOCK3V_M15
+        prob, f = oracle.shock3v_problem(**w3)
+        k = max(1, int(2.0e8 // (prob.ncell * prob.nv)))
+
+        def run():
+            t0 = time.perf_counter()
+            oracle.step3v(prob, f, k)
+            return time.perf_counter() - t0, oracle.threads()
+        return f"{k} time steps of {w3['name']}", prob.ncell * prob.nv * k, run, w3["name"]
+    if name == "adjoint":
+        wa = W.CAVITY_128
+        prob0, _, _ = oracle.cavity_problem(**wa)
+        xi = W.perturbation(wa.get("seed", 0), prob0.ncell, prob0.nv)
+        prob, g, h = oracle.cavity_problem(**wa, xi=xi)
+        k = 2
+
+        def run():
+            t0 = time.perf_counter()
+            oracle.adjoint_lid_shear(prob, g, h, k)
+            return time.perf_counter() - t0, oracle.threads()
+        return (f"oracle forward + reverse pass over {k} time steps of {wa['name']}", prob.ncell * prob.nv * k,
+                run, f"adjoint_{wa['name']}")
+    if name == "batch":
+        probs = []
+        for w_ in W.batch_instances(0)[::4]:  # every fourth instance, one time step each
+            if w_["kind"] == "shock":
+                prob, g, h = oracle.shock_problem(**w_)
+            else:
+                prob0, _, _ = oracle.cavity_problem(**w_)
+                xi = W.perturbation(w_.get("seed", 0), prob0.ncell, prob0.nv)
+                prob, g, h = oracle.cavity_problem(**w_, xi=xi)
+            probs.append((prob, g, h))
+        pts = sum(p.ncell * p.nv for p, _, _ in probs)
+
+        def run():
+            t0 = time.perf_counter()
+            for prob, g, h in probs:
+                oracle.step(prob, g, h, 1)
+            return time.perf_counter() - t0, oracle.threads()
+        return (f"one time step of every fourth batch instance ({len(probs)} instances)", pts, run,
+                "batch_64_cavities_16_shocks_seed0")
+    ncell, nv, _ = sizes(w)
+    k = max(1, int(2.0e8 // (ncell * nv)))  # a few seconds per sample
+
+    def run():
+        _, dt, threads = oracle_sample(w, k)
+        return dt, threads
+    return f"{k} time steps of {w['name']}", ncell * nv * k, run, w["name"]
+
+
 def reference_arm(args, w, rank, pg):
+    """The oracle as it stands, on the host cores, on bounded samples of the
+    workload (rank 0 only; other ranks exit without work)."""
     if rank != 0:
         return
-    ncell, nv, dim = sizes(w)
-    sample_steps = max(1, int(2.0e8 // (ncell * nv)))  # a few seconds per sample
+    label, updates, run, wname = reference_sampler(args.workload, w)
     for _ in range(args.warmup):
-        oracle_sample(w, max(1, sample_steps // 4))
-    times = []
-    rate = threads = None
+        run()
+    times, threads = [], None
     for _ in range(args.steps):
-        rate, dt, threads = oracle_sample(w, sample_steps)
+        dt, threads = run()
         times.append(dt)
     total = sum(times)
-    value = ncell * nv * sample_steps * args.steps / total
+    value = updates * args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w["name"], "sample_time_steps": sample_steps},
+        "data": "synthetic", "config": {"workload": wname, "sample": label},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{sample_steps} time steps of {w['name']} per benchmark step"},
+                         "sample": f"{label} per benchmark step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -698,7 +756,12 @@ def main():
     w = workload(args.workload) if args.workload not in ("batch", "adjoint", "shock3v", "shock3v_m15") else None
     if args.time_steps is not None and w is not None:
         w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
-    if args.workload in ("shock3v", "shock3v_m15") and args.impl != "reference":
+    if args.impl == "reference":
+        reference_arm(args, w, rank, pg)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    if args.workload in ("shock3v", "shock3v_m15"):
         from paper_0903_4044_gb300 import workloads as W
 
         w3 = W.SHOCK3V_M3 if args.workload == "shock3v" else W.SHOCK3V_M15
@@ -716,8 +779,6 @@ def main():
     if args.accuracy:
         if rank == 0:
             accuracy_arm(args, w)
-    elif args.impl == "reference":
-        reference_arm(args, w, rank, pg)
     else:
         ours_arm(args, w, world, rank, local, pg)
     if pg is not None:
