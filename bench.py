@@ -233,6 +233,7 @@ def reference_sampler(name: str, w: dict | None):
     if name == "batch":
         probs = []
         for w_ in W.batch_instances(0)[::4]:  # every fourth instance, one time step each
+            w_ = dict(w_, steps=1)
             if w_["kind"] == "shock":
                 prob, g, h = oracle.shock_problem(**w_)
             else:
