@@ -110,19 +110,22 @@ def test_integer_courant_streaming_is_an_exact_shift():
     # c_x = +-0.5, +-1.5, ... and dt/dx = 2: every Courant number is an odd
     # integer, so Eq. (exact) moves each velocity by whole cells
     nvx = 6
+    # (different inflow states at the two ends: sources beyond each end
+    # must read that end's Maxwellian)
+    left, right = (1, 0, 0, 0, 1), (1.3, 0.2, 0, 0, 0.8)
     cfg = oracle.make_config3v(nx=20, lx=20.0, nv=(nvx, 2, 2), vmin=(-3.0, -1.0, -1.0), vmax=(3.0, 1.0, 1.0),
-                               dt=2.0, inflow=((1, 0, 0, 0, 1), (1, 0, 0, 0, 1)))
+                               dt=2.0, inflow=(left, right))
     prob = oracle.Problem3v(cfg)
     rng = np.random.default_rng(5)
     f = rng.random((20, prob.nv))
     ft = oracle.stream3v(prob, f)
     cx = oracle.velocities3v(prob)[0]
-    gl = oracle.maxwellian3v(prob, (1, 0, 0, 0, 1))
+    gl, gr = oracle.maxwellian3v(prob, left), oracle.maxwellian3v(prob, right)
     for j in range(prob.nv):
         s = int(round(cx[j % nvx] * 2.0))
         for i in range(20):
             src = i - s
-            want = gl[j] if (src < 0 or src >= 20) else f[src, j]
+            want = gl[j] if src < 0 else gr[j] if src >= 20 else f[src, j]
             assert ft[i, j] == want
 
 
