@@ -70,6 +70,8 @@ struct bgk_solver {
   float4* m_coef = nullptr;
   float* m_cx = nullptr;
   float* m_cy = nullptr;
+  float* m_ax = nullptr;
+  float* m_ay = nullptr;
   float2* m_ghost = nullptr;
   float2* m_mabs = nullptr;
   double* m_sums = nullptr;  // [12]: mabs sums, emitted, mabs sums as float-float pairs
@@ -98,6 +100,8 @@ struct bgk_solver {
     M.vinfo = vinfo;
     M.cx = m_cx;
     M.cy = m_cy;
+    M.ax = m_ax;
+    M.ay = m_ay;
     M.ghost = m_ghost;
     M.mabs = m_mabs;
     M.mabs_sums = m_sums;
@@ -289,6 +293,10 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
 // CTA (measured best on 64^2 x 32^2 and 256^2 x 48^2 cavities).
 int auto_tile(const bgk::Params& P, int prec, int sms) {
   const long long ncell = (long long)P.nx * P.ny;
+  // FP32, 2D, at least 3 groups of 4 velocities per streaming thread: the
+  // pipelined one-cell kernel (measured 9 % faster than 2 cells per CTA on
+  // 256^2 x 48^2; slower on 64^2 x 32^2 and in BF16)
+  if (prec == BGK_F32 && P.dim == 2 && bgk::mixed_pipe_preferred(P) && ncell >= 2LL * sms) return 1;
   for (int t : {8, 4, 2}) {
     if (prec == BGK_F64 && t > 4) continue;
     // reduced precisions: at most 24 velocities per lane (instantiated)
@@ -312,7 +320,7 @@ void release(bgk_solver* s) {
     if (g) cudaGraphExecDestroy(g);
   void* bufs[] = {s->f[0], s->f[1], s->stage, s->mom_step, s->mom_tmp, s->flux_tmp, s->cx, s->cy,
                   s->coef, s->shift, s->cxy, s->vinfo, s->ghost, s->emitted, s->m_coef, s->m_cx,
-                  s->m_cy, s->m_ghost, s->m_mabs, s->m_sums, s->err};
+                  s->m_cy, s->m_ax, s->m_ay, s->m_ghost, s->m_mabs, s->m_sums, s->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -491,6 +499,8 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
     ALLOC(m_coef, P.nv);
     ALLOC(m_cx, P.nvx);
     ALLOC(m_cy, P.nvy);
+    ALLOC(m_ax, P.nvx);
+    ALLOC(m_ay, P.nvy);
     ALLOC(m_ghost, (size_t)bgk::kFaces * P.nv);
     ALLOC(m_mabs, P.nv);
     ALLOC(m_sums, 12);

@@ -60,6 +60,8 @@ struct MixedTables {
   const int* vinfo;         // [nv] as Tables::vinfo
   const float* cx;          // [nvx]
   const float* cy;          // [nvy]
+  const float* ax;          // [nvx] 2D flux-form weight |c_x| dt / dx per column (= coef.x)
+  const float* ay;          // [nvy] |c_y| dt / dy per row (= coef.y)
   const float2* ghost;      // [kFaces][nv] FP32 boundary Maxwellians
   const float2* mabs;       // [nv] absolute Maxwellian (n = 1, U = 0, theta = 1) in FP32
   const double* mabs_sums;  // [4] FP64 sums of mabs: g, c_x g, c_y g, |c|^2 g + h
@@ -163,6 +165,9 @@ cudaError_t launch_adj_step(const Params& P, const Tables& T, const double2* fn1
 cudaError_t launch_msum_moments(const Params& P, int prec, const MixedTables& M, const float2* msum,
                                 double4_32a* mom, cudaStream_t stream);
 cudaError_t prepare_step_mixed(const Params& P, int prec);
+// True when tile 1 runs the pipelined kernel with at least 3 groups of 4
+// velocities per streaming thread (FP32 state, 2D).
+bool mixed_pipe_preferred(const Params& P);
 cudaError_t launch_step_mixed(const Params& P, int prec, const MixedTables& M, const void* fin, void* fout,
                               double4_32a* mom, int* err, cudaStream_t stream);
 cudaError_t launch_to_f64(const Params& P, int prec, const MixedTables& M, const void* f, double2* out,

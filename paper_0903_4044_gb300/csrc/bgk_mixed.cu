@@ -179,15 +179,37 @@ struct CellCtx {
   float nw[4];
 };
 
+// The flux form of A1 for the 4 velocities of a group (row jy, columns
+// jx0..jx0+3; vi = vinfo of its first velocity) from their own and upwind
+// values; the weights come from the per-axis tables (one 16-byte load for
+// the 4 columns).
+__device__ __forceinline__ void flux_form(const MixedTables& M, int vi, const float2 (&f0)[4],
+                                          const float2 (&fx)[4], const float2 (&fy)[4], float2 (&ft)[4]) {
+  const float4 a4 = *reinterpret_cast<const float4*>(M.ax + vi_jx(vi));
+  const float ax[4] = {a4.x, a4.y, a4.z, a4.w};
+  const float ay = M.ay[vi_jy(vi)];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    ft[p].x = fmaf(-ay, f0[p].x - fy[p].x, fmaf(-ax[p], f0[p].x - fx[p].x, f0[p].x));
+    ft[p].y = fmaf(-ay, f0[p].y - fy[p].y, fmaf(-ax[p], f0[p].y - fx[p].y, f0[p].y));
+  }
+}
+
+__device__ __forceinline__ void unpack_f32(const float4& lo, const float4& hi, float2 (&v)[4]) {
+  v[0] = make_float2(lo.x, lo.y);
+  v[1] = make_float2(lo.z, lo.w);
+  v[2] = make_float2(hi.x, hi.y);
+  v[3] = make_float2(hi.z, hi.w);
+}
+
 // A1 for the 4 velocities j0..j0+3 of one cell, flux form
 //   f~ = f - ax (f - f_upx) - ay (f - f_upy)
 // in the stored representation (deviations for BF16).
 template <int PREC>
 __device__ __forceinline__ void stream_group(const Params& P, const MixedTables& M, const void* fin,
-                                             const CellCtx& C, int j0, float2 (&ft)[4]) {
+                                             const CellCtx& C, int j0, int vi, float2 (&ft)[4]) {
   using S = Store<PREC>;
   const int nv = P.nv;
-  const int vi = M.vinfo[j0];
   const int sgx = vi_sx(vi), sgy = vi_sy(vi);
   float2 f0[4], fx[4], fy[4];
   S::load4(fin, C.c0 + j0, f0);
@@ -218,11 +240,66 @@ __device__ __forceinline__ void stream_group(const Params& P, const MixedTables&
       for (int p = 0; p < 4; ++p) fy[p] = ghost_m<PREC>(P, M, face, j0 + p, nw, fin, C.c0);
     }
   }
+  flux_form(M, vi, f0, fx, fy, ft);
+}
+
+// A2 for the 4 velocities j0..j0+3: their contributions to (sum g,
+// sum c_x g, sum c_y g, sum |c|^2 g + h) in the lane's Kahan sums.
+__device__ __forceinline__ void group_sums(const MixedTables& M, int vi, const float2 (&ft)[4], float (&hs)[4],
+                                           float (&cs)[4]) {
+  const float4 c4 = *reinterpret_cast<const float4*>(M.cx + vi_jx(vi));
+  const float cx[4] = {c4.x, c4.y, c4.z, c4.w};
+  const float cy = M.cy[vi_jy(vi)];
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    const float4 co = M.coef[j0 + p];  // (ax, ay, cx, cy)
-    ft[p].x = fmaf(-co.y, f0[p].x - fy[p].x, fmaf(-co.x, f0[p].x - fx[p].x, f0[p].x));
-    ft[p].y = fmaf(-co.y, f0[p].y - fy[p].y, fmaf(-co.x, f0[p].y - fx[p].y, f0[p].y));
+    const float c2 = fmaf(cx[p], cx[p], cy * cy);
+    p0 += ft[p].x;
+    p1 = fmaf(cx[p], ft[p].x, p1);
+    p2 = fmaf(cy, ft[p].x, p2);
+    p3 = fmaf(c2, ft[p].x, p3) + ft[p].y;
+  }
+  kahan(hs[0], cs[0], p0);
+  kahan(hs[1], cs[1], p1);
+  kahan(hs[2], cs[2], p2);
+  kahan(hs[3], cs[3], p3);
+}
+
+// A1 + A2 for the 4 velocities j0..j0+3: f~ into ft, their contributions
+// to the lane's Kahan sums.
+template <int PREC>
+__device__ __forceinline__ void stream_sum_group(const Params& P, const MixedTables& M, const void* fin,
+                                                 const CellCtx& C, int j0, float2 (&ft)[4], float (&hs)[4],
+                                                 float (&cs)[4]) {
+  const int vi = M.vinfo[j0];
+  stream_group<PREC>(P, M, fin, C, j0, vi, ft);
+  group_sums(M, vi, ft, hs, cs);
+}
+
+// A4 for the 4 velocities j0..j0+3: r holds f~ (stored representation) and
+// becomes f~ + (a Phi - a f~), Phi_g = px[jx] py[jy] (the factors carry
+// a n / (pi theta)), Phi_h = kappa Phi_g.
+template <int PREC>
+__device__ __forceinline__ void relax_group(const MixedTables& M, const float* px, const float* py, int j0,
+                                            float a, float kappa, float2 (&r)[4]) {
+  const int vi = M.vinfo[j0];
+  const float4 xv = *reinterpret_cast<const float4*>(px + vi_jx(vi));
+  const float yv = py[vi_jy(vi)];
+  const float ph[4] = {xv.x * yv, xv.y * yv, xv.z * yv, xv.w * yv};
+  float2 mb[4];
+  if (Store<PREC>::delta) {
+    const float4* m4 = reinterpret_cast<const float4*>(M.mabs + j0);
+    unpack_f32(m4[0], m4[1], mb);
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    float fg = r[p].x, fh = r[p].y;  // full f~ for the a f~ term
+    if (Store<PREC>::delta) {
+      fg += mb[p].x;
+      fh += mb[p].y;
+    }
+    r[p].x += fmaf(-a, fg, ph[p]);
+    r[p].y += fmaf(-a, fh, kappa * ph[p]);
   }
 }
 
@@ -520,24 +597,7 @@ __device__ __forceinline__ void mixed2d_block(const Params& P, const MixedTables
 #pragma unroll
     for (int k = 0; k < MGL; ++k) {
       const int g = lic + k * 32 * WPC;
-      if (g < ngroups) {
-        const int j0 = 4 * g;
-        stream_group<PREC>(P, M, fin, C, j0, ft[k]);
-        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const float4 co = M.coef[j0 + p];
-          const float c2 = fmaf(co.z, co.z, co.w * co.w);
-          p0 += ft[k][p].x;
-          p1 = fmaf(co.z, ft[k][p].x, p1);
-          p2 = fmaf(co.w, ft[k][p].x, p2);
-          p3 = fmaf(c2, ft[k][p].x, p3) + ft[k][p].y;
-        }
-        kahan(hs[0], cs[0], p0);
-        kahan(hs[1], cs[1], p1);
-        kahan(hs[2], cs[2], p2);
-        kahan(hs[3], cs[3], p3);
-      }
+      if (g < ngroups) stream_sum_group<PREC>(P, M, fin, C, 4 * g, ft[k], hs, cs);
     }
     float ls[4];
 #pragma unroll
@@ -600,23 +660,7 @@ __device__ __forceinline__ void mixed2d_block(const Params& P, const MixedTables
     if (g < ngroups) {
       const int j0 = 4 * g;
       float2 r[4] = {ft[k][0], ft[k][1], ft[k][2], ft[k][3]};
-      if (ok) {
-        const int vi = M.vinfo[j0];
-        const float4 xv = *reinterpret_cast<const float4*>(px + vi_jx(vi));
-        const float yv = py[vi_jy(vi)];
-        const float ph[4] = {xv.x * yv, xv.y * yv, xv.z * yv, xv.w * yv};
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          float fg = r[p].x, fh = r[p].y;  // full f~ for the a f~ term
-          if (Store<PREC>::delta) {
-            const float2 m = M.mabs[j0 + p];
-            fg += m.x;
-            fh += m.y;
-          }
-          r[p].x += fmaf(-a, fg, ph[p]);
-          r[p].y += fmaf(-a, fh, kappa * ph[p]);
-        }
-      }
+      if (ok) relax_group<PREC>(M, px, py, j0, a, kappa, r);
       store_result<PREC>(fout, C.c0 + j0, r);
     }
   }
@@ -632,6 +676,152 @@ __global__ void __launch_bounds__(256, (PREC == PREC_F32 && MGL >= 6) ? 2 : 3)
   extern __shared__ float4 smemf4[];
   __shared__ MixedShared<G> S;
   mixed2d_block<PREC, G, MGL>(P, M, fin, fout, msum, err, blockIdx.x, reinterpret_cast<float*>(smemf4), S);
+}
+
+// ---- 2D, one cell at a time, pipelined ----------------------------------------
+// A resident CTA of 8 streaming warps and two parameter warps walks over the
+// cells blockIdx.x, blockIdx.x + gridDim.x, ...  The streaming warps stream
+// cell i+1 (A1 + A2) while a parameter warp solves cell i's parameters
+// (phase 2); they then relax cell i (A4) from its buffer.  The two
+// parameter warps take the cells in turn, each owning one buffer of each
+// kind (f~, partial sums, factors), so each has two cells' time for its
+// serial phase.  Named barriers hand the sums over (ids 1, 2: the 256
+// streaming threads arrive, the owning parameter warp waits) and the
+// factors back (ids 3, 4: that warp arrives, the 256 wait).
+//
+// Every value is computed as in the one-cell block (same velocity-to-thread
+// map, same summation order), so the two give identical states; the
+// persistent batch kernel runs the block.
+constexpr int kPipeMath = 2;
+constexpr int kPipeThreads = 32 * (8 + kPipeMath);
+constexpr int kPipeBar = 32 * 9;  // threads at each named barrier: 8 streaming warps + one parameter warp
+constexpr size_t kPipeMaxSmem = 72 * 1024;  // dynamic shared memory of one pipelined CTA at most (3 per SM)
+
+// Barrier ids as immediates (a register id would reserve all 16).
+__device__ __forceinline__ void bar_sync_id(int id) {
+  switch (id) {
+    case 1: asm volatile("bar.sync 1, %0;" ::"n"(kPipeBar) : "memory"); break;
+    case 2: asm volatile("bar.sync 2, %0;" ::"n"(kPipeBar) : "memory"); break;
+    case 3: asm volatile("bar.sync 3, %0;" ::"n"(kPipeBar) : "memory"); break;
+    default: asm volatile("bar.sync 4, %0;" ::"n"(kPipeBar) : "memory"); break;
+  }
+}
+__device__ __forceinline__ void bar_arrive_id(int id) {
+  switch (id) {
+    case 1: asm volatile("bar.arrive 1, %0;" ::"n"(kPipeBar) : "memory"); break;
+    case 2: asm volatile("bar.arrive 2, %0;" ::"n"(kPipeBar) : "memory"); break;
+    case 3: asm volatile("bar.arrive 3, %0;" ::"n"(kPipeBar) : "memory"); break;
+    default: asm volatile("bar.arrive 4, %0;" ::"n"(kPipeBar) : "memory"); break;
+  }
+}
+
+// Dynamic shared memory: float4 f~[2 buffers][2 planes][nv / 4] (plane 0
+// holds velocities 0, 1 of a group of 4 and plane 1 velocities 2, 3, so
+// consecutive threads touch consecutive words), then float factors[2][nvx + nvy].
+__host__ __device__ __forceinline__ size_t pipe_smem_bytes(const Params& P) {
+  return sizeof(float4) * 4 * (size_t)(P.nv / 4) + ((sizeof(float) * 2 * (size_t)(P.nvx + P.nvy) + 15) & ~(size_t)15);
+}
+
+template <int PREC, int MGL>
+__global__ void __launch_bounds__(kPipeThreads, 3)
+    step_mixed_pipe_kernel(const void* __restrict__ fin, void* __restrict__ fout, float2* __restrict__ msum,
+                           const Params P, const MixedTables M, int* __restrict__ err) {
+  extern __shared__ float4 smemf4[];
+  __shared__ float2 s_part[2][8][4];
+  __shared__ CellPar s_cp[2];
+  const int ngroups = P.nv >> 2;
+  const int nf = P.nvx + P.nvy;
+  const int ncell = P.nx * P.ny;
+  float* fac = reinterpret_cast<float*>(smemf4 + 4 * ngroups);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp >= 8) {  // phase 2 of every second cell, buffer m
+    const int m = warp - 8;
+    float* px = fac + m * nf;
+    float* py = px + P.nvx;
+    for (int cell = blockIdx.x + m * gridDim.x; cell < ncell; cell += kPipeMath * gridDim.x) {
+      bar_sync_id(1 + m);
+      CellPar cp;
+      cell_moments<PREC, 8>(P, M, cell, 0, s_part[m], cp, msum);
+      // the Gaussians in chunks of 32 as the block's 8 warps take them,
+      // each chunk's central sums totalled over the warp, chunks in order
+      float Mx[5], My[5];
+      for (int w = 0; w < 8 && 32 * w < nf; ++w) {
+        float ax[5], ay[5];
+        cell_gauss<8>(P, M, w, cp, px, py, ax, ay);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          ax[k] = warp_sum_f(ax[k]);
+          ay[k] = warp_sum_f(ay[k]);
+          Mx[k] = w == 0 ? ax[k] : Mx[k] + ax[k];
+          My[k] = w == 0 ? ay[k] : My[k] + ay[k];
+        }
+      }
+      cell_effective(P, cp, Mx, My);
+      if (cp.ok) cell_factors<1>(P, M, 0, cp, px, py);
+      if (lane == 0) {
+        s_cp[m] = cp;
+        if (!cp.ok) atomicOr(err, ERR_MOMENT);
+      }
+      __syncwarp();
+      bar_arrive_id(3 + m);
+    }
+    return;
+  }
+
+  const int tid = threadIdx.x;
+  int b = 0;
+  size_t prev_c0 = 0;
+  bool have_prev = false;
+  for (int cell = blockIdx.x;; cell += gridDim.x) {
+    const bool live = cell < ncell;
+    if (live) {  // A1 + A2 of this cell into buffer b
+      const CellCtx C = cell_ctx<PREC>(P, M, fin, cell);
+      float4* flo = smemf4 + (size_t)(2 * b) * ngroups;
+      float4* fhi = flo + ngroups;
+      float hs[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < MGL; ++k) {
+        const int g = tid + 256 * k;
+        if (g < ngroups) {
+          float2 ft[4];
+          stream_sum_group<PREC>(P, M, fin, C, 4 * g, ft, hs, cs);
+          flo[g] = make_float4(ft[0].x, ft[0].y, ft[1].x, ft[1].y);
+          fhi[g] = make_float4(ft[2].x, ft[2].y, ft[3].x, ft[3].y);
+        }
+      }
+      float ls[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ls[k] = -cs[k];
+      float oh, ol;
+      warp_reduce4_ff(hs, ls, oh, ol);
+      if ((lane & 7) == 0) s_part[b][warp][lane >> 3] = make_float2(oh, ol);
+      bar_arrive_id(1 + b);
+    }
+    if (have_prev) {  // A4 of the previous cell from buffer b ^ 1
+      const int pb = b ^ 1;
+      bar_sync_id(3 + pb);
+      const CellPar cp = s_cp[pb];
+      const float* px = fac + pb * nf;
+      const float* py = px + P.nvx;
+      const float4* flo = smemf4 + (size_t)(2 * pb) * ngroups;
+      const float4* fhi = flo + ngroups;
+#pragma unroll
+      for (int k = 0; k < MGL; ++k) {
+        const int g = tid + 256 * k;
+        if (g < ngroups) {
+          float2 r[4];
+          unpack_f32(flo[g], fhi[g], r);
+          if (cp.ok) relax_group<PREC>(M, px, py, 4 * g, cp.a, cp.kappa, r);
+          store_result<PREC>(fout, prev_c0 + 4 * g, r);
+        }
+      }
+    }
+    if (!live) break;
+    have_prev = true;
+    prev_c0 = (size_t)cell * P.nv;
+    b ^= 1;
+  }
 }
 
 // ---- 1D, FP32 state ---------------------------------------------------------
@@ -957,7 +1147,7 @@ cudaError_t launch_msum_moments(const Params& P, int prec, const MixedTables& M,
 // the FP64 sums that pin the mixed form's moments and wall fluxes to the
 // values actually stored.
 __global__ void mixed_tables_kernel(const Params P, const Tables T, float4* coef, float* cx, float* cy,
-                                    float2* ghost, float2* mabs) {
+                                    float* ax, float* ay, float2* ghost, float2* mabs) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P.nv) return;
   const int jx = j % P.nvx, jy = j / P.nvx;
@@ -966,6 +1156,8 @@ __global__ void mixed_tables_kernel(const Params P, const Tables T, float4* coef
   coef[j] = make_float4((float)c.y, (float)c.z, (float)v.x, (float)v.y);
   if (jy == 0) cx[jx] = (float)v.x;
   if (jx == 0) cy[jy] = (float)v.y;
+  if (jy == 0) ax[jx] = (float)c.y;  // 2D: |c_x| dt / dx depends on jx alone
+  if (jx == 0) ay[jy] = (float)c.z;  //     |c_y| dt / dy on jy alone
   for (int face = 0; face < kFaces; ++face) {
     const double2 g = T.ghost[face * P.nv + j];
     ghost[face * P.nv + j] = make_float2((float)g.x, (float)g.y);
@@ -1008,7 +1200,8 @@ cudaError_t launch_build_mixed_tables(const Params& P, const Tables& T, const Mi
                                       cudaStream_t stream) {
   mixed_tables_kernel<<<(P.nv + 255) / 256, 256, 0, stream>>>(
       P, T, const_cast<float4*>(M.coef), const_cast<float*>(M.cx), const_cast<float*>(M.cy),
-      const_cast<float2*>(M.ghost), const_cast<float2*>(M.mabs));
+      const_cast<float*>(M.ax), const_cast<float*>(M.ay), const_cast<float2*>(M.ghost),
+      const_cast<float2*>(M.mabs));
   mixed_sums_kernel<<<1, 256, 0, stream>>>(P, M, const_cast<double*>(M.mabs_sums),
                                            const_cast<float2*>(M.mabs_ff), const_cast<double*>(M.emitted));
   return cudaGetLastError();
@@ -1091,11 +1284,49 @@ cudaError_t dispatch_mgl(const Params& P, const MixedTables& M, const void* fin,
   return cudaErrorInvalidValue;
 }
 
+// Groups of 4 velocities per streaming thread of the pipelined kernel (at
+// most 4: a cell has at most 4096 velocities); 0 if more.
+int pipe_groups(const Params& P) {
+  const int need = (P.nv / 4 + 255) / 256;
+  return need <= 4 ? need : 0;
+}
+
+template <int PREC, int MGL>
+cudaError_t launch_pipe(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
+                        int* err, cudaStream_t stream) {
+  const size_t smem = pipe_smem_bytes(P);
+  int dev = 0, per_sm = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_mixed_pipe_kernel<PREC, MGL>, kPipeThreads, smem);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int ncell = P.nx * P.ny;
+  const int grid = per_sm * sms < ncell ? per_sm * sms : ncell;
+  step_mixed_pipe_kernel<PREC, MGL><<<grid, kPipeThreads, smem, stream>>>(fin, fout, msum, P, M, err);
+  return cudaGetLastError();
+}
+
+// Tile 1: the pipelined kernel when its buffers fit, else the one-cell block
+// (the same arithmetic).
+template <int PREC>
+cudaError_t dispatch_tile1(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
+                           int* err, cudaStream_t stream) {
+  if (pipe_smem_bytes(P) <= kPipeMaxSmem) switch (pipe_groups(P)) {
+      case 1: return launch_pipe<PREC, 1>(P, M, fin, fout, msum, err, stream);
+      case 2: return launch_pipe<PREC, 2>(P, M, fin, fout, msum, err, stream);
+      case 3: return launch_pipe<PREC, 3>(P, M, fin, fout, msum, err, stream);
+      case 4: return launch_pipe<PREC, 4>(P, M, fin, fout, msum, err, stream);
+    }
+  return dispatch_mgl<PREC, 1>(P, M, fin, fout, msum, err, stream);
+}
+
 template <int PREC>
 cudaError_t dispatch_m(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
                        int* err, cudaStream_t stream) {
   switch (P.tile) {
-    case 1: return dispatch_mgl<PREC, 1>(P, M, fin, fout, msum, err, stream);
+    case 1: return dispatch_tile1<PREC>(P, M, fin, fout, msum, err, stream);
     case 2: return dispatch_mgl<PREC, 2>(P, M, fin, fout, msum, err, stream);
     case 4: return dispatch_mgl<PREC, 4>(P, M, fin, fout, msum, err, stream);
     case 8: return dispatch_mgl<PREC, 8>(P, M, fin, fout, msum, err, stream);
@@ -1104,6 +1335,10 @@ cudaError_t dispatch_m(const Params& P, const MixedTables& M, const void* fin, v
 }
 
 }  // namespace
+
+bool mixed_pipe_preferred(const Params& P) {
+  return P.dim == 2 && pipe_smem_bytes(P) <= kPipeMaxSmem && pipe_groups(P) >= 3;
+}
 
 size_t step_mixed_smem_bytes(const Params& P, int tile, int prec) { return mixed_smem(P, tile, prec); }
 
@@ -1118,7 +1353,26 @@ int mixed_groups_per_lane(const Params& P, int tile) {
   return 0;
 }
 
-cudaError_t prepare_step_mixed(const Params&, int) { return cudaSuccess; }
+// The attribute belongs to the kernel: set it once to the pipelined
+// kernel's largest buffers, whatever solver asks first.
+cudaError_t prepare_step_mixed(const Params&, int) {
+  static cudaError_t done = [] {
+    cudaError_t e = cudaSuccess;
+    auto set = [&e](const void* fn) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeMaxSmem);
+    };
+    set((const void*)step_mixed_pipe_kernel<PREC_F32, 1>);
+    set((const void*)step_mixed_pipe_kernel<PREC_F32, 2>);
+    set((const void*)step_mixed_pipe_kernel<PREC_F32, 3>);
+    set((const void*)step_mixed_pipe_kernel<PREC_F32, 4>);
+    set((const void*)step_mixed_pipe_kernel<PREC_BF16, 1>);
+    set((const void*)step_mixed_pipe_kernel<PREC_BF16, 2>);
+    set((const void*)step_mixed_pipe_kernel<PREC_BF16, 3>);
+    set((const void*)step_mixed_pipe_kernel<PREC_BF16, 4>);
+    return e;
+  }();
+  return done;
+}
 
 cudaError_t launch_step_mixed(const Params& P, int prec, const MixedTables& M, const void* fin, void* fout,
                               double4_32a* mom, int* err, cudaStream_t stream) {

@@ -126,6 +126,31 @@ def test_persistent_equals_independent_solvers():
     b.close()
 
 
+def test_pipelined_tile1_equals_block():
+    # tile 1 of a single solver runs the pipelined kernel (one cell per
+    # iteration of a resident CTA, parameters on a ninth warp); the
+    # persistent kernel runs the one-cell block: the states must agree bit
+    # for bit (1, 3 and 4 velocity groups per thread, ragged ones included,
+    # fewer cells than resident CTAs, and more)
+    ws = [W.scaled(W.CAVITY_64, name="q0", n=13, nv=48, precision="f32", seed=5, tile_cells=1),
+          W.scaled(W.CAVITY_64, name="q1", n=37, nv=32, precision="f32", seed=6, tile_cells=1),
+          W.scaled(W.CAVITY_64, name="q2", n=5, nv=64, precision="f32", seed=7, tile_cells=1),
+          W.scaled(W.CAVITY_64, name="q3", n=9, nv=24, precision="f32", seed=8, tile_cells=1,
+                   wall="specular")]
+    b = solver.Batch(ws)
+    b.set_persistent(True)
+    assert [int(s.info.tile_cells) for s in b.solvers] == [1] * len(ws)
+    b.step(23)
+    b.sync()
+    for w, sb in zip(ws, b.solvers):
+        s = _single(w)
+        s.step(23)
+        assert np.array_equal(sb.get_state(), s.get_state()), w["name"]
+        assert np.array_equal(sb.moments(which=1), s.moments(which=1)), w["name"]
+        s.close()
+    b.close()
+
+
 def test_persistent_needs_fp32():
     b = solver.Batch(MIX[:2])
     with pytest.raises(B.BgkError) as e:

@@ -123,6 +123,25 @@ def test_mixed_variants_and_tiles(name):
         s.close()
 
 
+@pytest.mark.parametrize("name", ["f32", "bf16"])
+def test_mixed_tile1_large_velocity_grid(name):
+    # 56 x 56 velocities: four groups of four per streaming thread of the
+    # pipelined tile-1 kernel (the last ragged), fewer cells than CTAs
+    w = W.scaled(W.CAVITY_64, n=6, nv=56, amp=1e-2, tile_cells=1)
+    s, prob, g, h = _pair(w, PRECS[name])
+    assert s.info.tile_cells == 1
+    s.step(2)
+    g1, h1, _ = oracle.step(prob, g, h, 2)
+    st = s.get_state()
+    if name == "f32":
+        assert np.abs(st[..., 0] - g1).max() / np.abs(g1).max() < 4e-6
+        assert np.abs(st[..., 1] - h1).max() / np.abs(h1).max() < 4e-6
+    else:
+        Gm, _ = _mabs(prob)
+        assert np.abs(st[..., 0] - g1).max() < 3e-2 * np.abs(g1 - Gm).max() + 4e-6 * np.abs(g1).max()
+    s.close()
+
+
 def test_mixed_full_size_one_step():
     # The 256 x 256 x 48 x 48 grid in FP32 and BF16, one step, whole state.
     w = W.scaled(W.CAVITY_256)
