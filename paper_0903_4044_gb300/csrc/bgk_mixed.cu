@@ -86,24 +86,43 @@ __device__ __forceinline__ void warp_reduce4_ff(float (&h)[4], float (&l)[4], fl
 template <int PREC>
 struct Store;
 
+// FP32 storage order inside a cell's block (2D): the velocities come in
+// groups of 4 (one row, one sign of c_x and c_y) and the groups in chunks of
+// 32; a chunk of cs groups stores the first two velocities of each group
+// (16 bytes, group after group), then the last two.  The 32 lanes of a warp
+// take the 32 groups of a chunk, so each 16-byte access of the warp covers
+// 512 contiguous bytes (4 L1 wavefronts) instead of 1 KB at a 32-byte
+// stride.  Offsets are in float2 units from the start of the cell's block.
+__host__ __device__ __forceinline__ int f32_half(int g, int ngroups, int half) {
+  const int q = g >> 5, cs = min(32, ngroups - 32 * q);
+  return 128 * q + 2 * (g & 31) + half * 2 * cs;
+}
+__host__ __device__ __forceinline__ int f32_pos(int j, int ngroups) {
+  return f32_half(j >> 2, ngroups, (j >> 1) & 1) + (j & 1);
+}
+
 template <>
 struct Store<PREC_F32> {
   static constexpr bool delta = false;
-  __device__ static void load4(const void* base, size_t idx, float2 (&v)[4]) {
-    const float4* p = reinterpret_cast<const float4*>(static_cast<const float2*>(base) + idx);
-    const float4 a = __ldg(p), b = __ldg(p + 1);
+  // the 4 velocities j0..j0+3 (j0 = 4 g) of the cell whose block starts at c0
+  __device__ static void load4(const void* base, size_t c0, int j0, int ng, float2 (&v)[4]) {
+    const float2* b = static_cast<const float2*>(base) + c0;
+    const int g = j0 >> 2;
+    const float4 a = __ldg(reinterpret_cast<const float4*>(b + f32_half(g, ng, 0)));
+    const float4 c = __ldg(reinterpret_cast<const float4*>(b + f32_half(g, ng, 1)));
     v[0] = make_float2(a.x, a.y);
     v[1] = make_float2(a.z, a.w);
-    v[2] = make_float2(b.x, b.y);
-    v[3] = make_float2(b.z, b.w);
+    v[2] = make_float2(c.x, c.y);
+    v[3] = make_float2(c.z, c.w);
   }
-  __device__ static void store4(void* base, size_t idx, const float2 (&v)[4]) {
-    float4* p = reinterpret_cast<float4*>(static_cast<float2*>(base) + idx);
-    p[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    p[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+  __device__ static void store4(void* base, size_t c0, int j0, int ng, const float2 (&v)[4]) {
+    float2* b = static_cast<float2*>(base) + c0;
+    const int g = j0 >> 2;
+    *reinterpret_cast<float4*>(b + f32_half(g, ng, 0)) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    *reinterpret_cast<float4*>(b + f32_half(g, ng, 1)) = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
   }
-  __device__ static float2 load1(const void* base, size_t idx) {
-    return __ldg(static_cast<const float2*>(base) + idx);
+  __device__ static float2 load1(const void* base, size_t c0, int j, int ng) {
+    return __ldg(static_cast<const float2*>(base) + c0 + f32_pos(j, ng));
   }
 };
 
@@ -121,19 +140,20 @@ struct Store<PREC_BF16> {
     memcpy(&w, &b, 4);
     return w;
   }
-  __device__ static void load4(const void* base, size_t idx, float2 (&v)[4]) {
-    const uint4 u = __ldg(reinterpret_cast<const uint4*>(static_cast<const unsigned*>(base) + idx));
+  // one 32-bit word per velocity in velocity order (ng unused)
+  __device__ static void load4(const void* base, size_t c0, int j0, int, float2 (&v)[4]) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(static_cast<const unsigned*>(base) + c0 + j0));
     v[0] = unpack(u.x);
     v[1] = unpack(u.y);
     v[2] = unpack(u.z);
     v[3] = unpack(u.w);
   }
-  __device__ static void store4(void* base, size_t idx, const float2 (&v)[4]) {
-    *reinterpret_cast<uint4*>(static_cast<unsigned*>(base) + idx) =
+  __device__ static void store4(void* base, size_t c0, int j0, int, const float2 (&v)[4]) {
+    *reinterpret_cast<uint4*>(static_cast<unsigned*>(base) + c0 + j0) =
         make_uint4(pack(v[0]), pack(v[1]), pack(v[2]), pack(v[3]));
   }
-  __device__ static float2 load1(const void* base, size_t idx) {
-    return unpack(__ldg(static_cast<const unsigned*>(base) + idx));
+  __device__ static float2 load1(const void* base, size_t c0, int j, int) {
+    return unpack(__ldg(static_cast<const unsigned*>(base) + c0 + j));
   }
 };
 
@@ -148,7 +168,7 @@ __device__ __forceinline__ float2 ghost_m(const Params& P, const MixedTables& M,
     const int jx = vi_jx(vi), jy = vi_jy(vi);
     const int jr = (face == XLO || face == XHI) ? jy * P.nvx + (P.nvx - 1 - jx)
                                                 : (P.nvy - 1 - jy) * P.nvx + jx;
-    return Store<PREC>::load1(fin, c0 + jr);  // M_abs is mirror symmetric
+    return Store<PREC>::load1(fin, c0, jr, P.nv >> 2);  // M_abs is mirror symmetric
   }
   float2 g = M.ghost[face * P.nv + j];
   if (kind == BC_DIFFUSE) g = make_float2(nw * g.x, nw * g.y);
@@ -212,13 +232,14 @@ __device__ __forceinline__ void stream_group(const Params& P, const MixedTables&
   const int nv = P.nv;
   const int sgx = vi_sx(vi), sgy = vi_sy(vi);
   float2 f0[4], fx[4], fy[4];
-  S::load4(fin, C.c0 + j0, f0);
+  const int ng = nv >> 2;
+  S::load4(fin, C.c0, j0, ng, f0);
   if (C.interior) {
-    S::load4(fin, C.c0 - (ptrdiff_t)sgx * nv + j0, fx);
-    S::load4(fin, C.c0 - (ptrdiff_t)sgy * (ptrdiff_t)C.row + j0, fy);
+    S::load4(fin, C.c0 - (ptrdiff_t)sgx * nv, j0, ng, fx);
+    S::load4(fin, C.c0 - (ptrdiff_t)sgy * (ptrdiff_t)C.row, j0, ng, fy);
   } else {
-    if (sgx > 0 && !C.bxlo) S::load4(fin, C.c0 - nv + j0, fx);
-    else if (sgx < 0 && !C.bxhi) S::load4(fin, C.c0 + nv + j0, fx);
+    if (sgx > 0 && !C.bxlo) S::load4(fin, C.c0 - nv, j0, ng, fx);
+    else if (sgx < 0 && !C.bxhi) S::load4(fin, C.c0 + nv, j0, ng, fx);
     else if (sgx == 0) {
 #pragma unroll
       for (int p = 0; p < 4; ++p) fx[p] = f0[p];
@@ -228,8 +249,8 @@ __device__ __forceinline__ void stream_group(const Params& P, const MixedTables&
 #pragma unroll
       for (int p = 0; p < 4; ++p) fx[p] = ghost_m<PREC>(P, M, face, j0 + p, nw, fin, C.c0);
     }
-    if (sgy > 0 && !C.bylo) S::load4(fin, C.c0 - C.row + j0, fy);
-    else if (sgy < 0 && !C.byhi) S::load4(fin, C.c0 + C.row + j0, fy);
+    if (sgy > 0 && !C.bylo) S::load4(fin, C.c0 - C.row, j0, ng, fy);
+    else if (sgy < 0 && !C.byhi) S::load4(fin, C.c0 + C.row, j0, ng, fy);
     else if (sgy == 0) {
 #pragma unroll
       for (int p = 0; p < 4; ++p) fy[p] = f0[p];
@@ -330,7 +351,7 @@ __device__ __forceinline__ CellCtx cell_ctx(const Params& P, const MixedTables& 
     float hs[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
     for (int j0 = 4 * lane; j0 < nv; j0 += 128) {
       float2 v[4];
-      S::load4(fin, C.c0 + j0, v);
+      S::load4(fin, C.c0, j0, nv >> 2, v);
       const int vi = M.vinfo[j0];
       float ax = 0.f, ay = 0.f;
 #pragma unroll
@@ -544,8 +565,9 @@ __device__ __forceinline__ unsigned bf16_sr(float x, unsigned salt) {
 }
 
 template <int PREC>
-__device__ __forceinline__ void store_result(void* fout, size_t idx, const float2 (&r)[4]) {
+__device__ __forceinline__ void store_result(void* fout, size_t c0, int j0, int ng, const float2 (&r)[4]) {
   if (PREC == PREC_BF16) {
+    const size_t idx = c0 + j0;
     unsigned w[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
@@ -554,7 +576,7 @@ __device__ __forceinline__ void store_result(void* fout, size_t idx, const float
     }
     *reinterpret_cast<uint4*>(static_cast<unsigned*>(fout) + idx) = make_uint4(w[0], w[1], w[2], w[3]);
   } else {
-    Store<PREC>::store4(fout, idx, r);
+    Store<PREC>::store4(fout, c0, j0, ng, r);
   }
 }
 
@@ -661,7 +683,7 @@ __device__ __forceinline__ void mixed2d_block(const Params& P, const MixedTables
       const int j0 = 4 * g;
       float2 r[4] = {ft[k][0], ft[k][1], ft[k][2], ft[k][3]};
       if (ok) relax_group<PREC>(M, px, py, j0, a, kappa, r);
-      store_result<PREC>(fout, C.c0 + j0, r);
+      store_result<PREC>(fout, C.c0, j0, ngroups, r);
     }
   }
 }
@@ -813,7 +835,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3)
           float2 r[4];
           unpack_f32(flo[g], fhi[g], r);
           if (cp.ok) relax_group<PREC>(M, px, py, 4 * g, cp.a, cp.kappa, r);
-          store_result<PREC>(fout, prev_c0 + 4 * g, r);
+          store_result<PREC>(fout, prev_c0, 4 * g, ngroups, r);
         }
       }
     }
@@ -1213,7 +1235,10 @@ __global__ void to_f64_kernel(const Params P, const MixedTables M, const void* f
   const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   const size_t total = (size_t)P.nx * P.ny * P.nv;
   if (idx >= total) return;
-  const float2 v = Store<PREC>::load1(f, idx);
+  const size_t c0 = idx - idx % P.nv;
+  const int j = (int)(idx % P.nv);
+  const float2 v = (PREC == PREC_F32 && P.dim == 1) ? static_cast<const float2*>(f)[idx]
+                                                    : Store<PREC>::load1(f, c0, j, P.nv >> 2);
   double2 r = make_double2((double)v.x, (double)v.y);
   if (Store<PREC>::delta) {
     const float2 m = M.mabs[idx % P.nv];
@@ -1230,7 +1255,8 @@ __global__ void from_f64_kernel(const Params P, const MixedTables M, const doubl
   if (idx >= total) return;
   double2 v = in[idx];
   if (PREC == PREC_F32) {
-    static_cast<float2*>(f)[idx] = make_float2((float)v.x, (float)v.y);
+    const size_t at = P.dim == 1 ? idx : idx - idx % P.nv + f32_pos((int)(idx % P.nv), P.nv >> 2);
+    static_cast<float2*>(f)[at] = make_float2((float)v.x, (float)v.y);
   } else {
     const float2 m = M.mabs[idx % P.nv];
     v.x -= (double)m.x;
