@@ -51,16 +51,20 @@ DETAIL = {"f64": "FP64 state and arithmetic",
 MEASURED_TRAFFIC = {
     ("cavity_kn0.1_ma0.1_64x64_v32x32_f64", "f64"): {
         "bytes": 166.4e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
-        "sha1": "46e7aee5143907e1289cffcf0def23afe676c5bd"},
+        "sha1": "46e7aee5143907e1289cffcf0def23afe676c5bd", "kernel": "bgk::step_f64_kernel"},
+    ("cavity_kn0.05_ma0.05_256x256_v48x48", "f32"): {
+        "bytes": 2.5448e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
+        "sha1": "14dd38416f0941d107eeef8f49ad6a0228f97a39", "kernel": "bgk::step_mixed_pipe_kernel"},
 }
 
 
-def measured_traffic(workload: str, precision: str):
-    """Captured DRAM bytes per launch for this workload, if the captured kernel is the one built."""
+def measured_traffic(workload: str, precision: str, kernel: str):
+    """Captured DRAM bytes per launch for this workload, if the captured kernel is the one built
+    and the one launched."""
     import hashlib
 
     rec = MEASURED_TRAFFIC.get((workload, precision))
-    if rec is None:
+    if rec is None or rec["kernel"] != kernel:
         return None
     h = hashlib.sha1()
     for f in rec["sources"]:
@@ -381,8 +385,13 @@ def ours_arm(args, w, world, rank, local, pg):
     else:
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peaks["source"]}
-    kname = "bgk::step_f64_kernel" if args.precision == "f64" else "bgk::step_mixed_kernel"
-    traffic = args.traffic if args.traffic is not None else measured_traffic(w["name"], args.precision)
+    if args.precision == "f64":
+        kname = "bgk::step_f64_kernel"
+    elif dim == 1:
+        kname = "bgk::step_mixed1d_kernel"
+    else:  # tile 1 of the 2D reduced-precision step is the pipelined kernel
+        kname = "bgk::step_mixed_pipe_kernel" if int(s.info.tile_cells) == 1 else "bgk::step_mixed_kernel"
+    traffic = args.traffic if args.traffic is not None else measured_traffic(w["name"], args.precision, kname)
     roof.update({"traffic": traffic, "kernel": kname,
                  "launch_ms": per_launch * 1e3, "hbm_gbs": hbm_achieved,
                  "hbm_frac": hbm_achieved / peaks["hbm_gbs"], "fp64_tflops": alu_achieved})

@@ -12,13 +12,13 @@
 // mass change is only the rounding of each term (no systematic drift from
 // weights that do not sum to 1).
 //
-// G cells per CTA, one warp per cell, each lane handling 4 consecutive
-// velocities (one row, one sign of c_x and c_y: the velocity grid has
-// nvx % 8 == 0 and sign changes on multiples of 4, checked on the host).
-// Unlike the FP64 kernel, f~ is not staged in shared memory: the FP32
-// streaming is recomputed in the relaxation pass from inputs that are still
-// in L1/L2, which keeps shared memory free for many resident warps (the FP32
-// arithmetic is cheap; shared-memory capacity per cell was the limit).
+// Each lane handles groups of 4 consecutive velocities (one row, one sign
+// of c_x and c_y: the velocity grid has nvx % 8 == 0 and sign changes on
+// multiples of 4, checked on the host).  Two kernels: a block of G cells per
+// CTA (8 / G warps per cell, f~ kept in registers between streaming and
+// relaxation), and for one cell per CTA a pipelined kernel that streams the
+// next cell while two extra warps solve the previous cell's parameters (f~
+// in shared memory).  Both run the same arithmetic in the same order.
 #include <cuda_bf16.h>
 
 #include "bgk_device.cuh"
