@@ -50,11 +50,11 @@ DETAIL = {"f64": "FP64 state and arithmetic",
 # null.  Captures and commands: profiles/step_f64_cavity64.md.
 MEASURED_TRAFFIC = {
     ("cavity_kn0.1_ma0.1_64x64_v32x32_f64", "f64"): {
-        "bytes": 166.4e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
-        "sha1": "46e7aee5143907e1289cffcf0def23afe676c5bd", "kernel": "bgk::step_f64_kernel"},
-    ("cavity_kn0.05_ma0.05_256x256_v48x48", "f32"): {
-        "bytes": 2.5448e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
-        "sha1": "14dd38416f0941d107eeef8f49ad6a0228f97a39", "kernel": "bgk::step_mixed_pipe_kernel"},
+        "bytes": 169.0e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
+        "sha1": "6161cceb9040c0d99beff2594a8ed3676a0d9198", "kernel": "bgk::step_f64_kernel"},
+    ("cavity_kn0.05_ma0.05_256x256_v48x48_200steps", "f32"): {
+        "bytes": 2.53e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
+        "sha1": "4f86d8788e3b61f3090d89fc0957a56b7487dc17", "kernel": "bgk::step_mixed_pipe_kernel"},
 }
 
 
@@ -764,7 +764,7 @@ def main():
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
     w = workload(args.workload) if args.workload not in ("batch", "adjoint", "shock3v", "shock3v_m15") else None
-    if args.time_steps is not None and w is not None:
+    if args.time_steps is not None and w is not None and args.time_steps != w["steps"]:
         w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
     if args.impl == "reference":
         reference_arm(args, w, rank, pg)

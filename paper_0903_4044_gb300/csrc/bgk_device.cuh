@@ -100,13 +100,13 @@ __device__ __forceinline__ double2 maxwell_point(int dim, const double p[4], dou
 __device__ __forceinline__ void moments_from_sums(double s0, double sx, double sy, double se,
                                                   double dv, double q[4]) {
   const double n = s0 * dv;
-  const double ux = sx * dv / n;
-  const double uy = sy * dv / n;
-  const double e = se * dv;
+  const double in = dv / n;  // one division
+  const double ux = sx * in;
+  const double uy = sy * in;
   q[0] = n;
   q[1] = ux;
   q[2] = uy;
-  q[3] = (2.0 / 3.0) * (e / n - (ux * ux + uy * uy));
+  q[3] = (2.0 / 3.0) * (se * in - (ux * ux + uy * uy));
 }
 
 __device__ __forceinline__ bool moments_ok(const double q[4]) {
@@ -132,12 +132,22 @@ __device__ __forceinline__ bool moments_ok(const double q[4]) {
 // ---------------------------------------------------------------------------
 struct EffState {
   double base[4], p[4];
+  double ib0, ith, isq;  // 1 / n_b, 1 / theta_b, 1 / sqrt(theta_b)
   int it;
   bool conv, fail, reeval;
 };
 
+// Reciprocals of the base point, taken once per base (the FP64 pipe
+// charges a division about ten instructions).
+__device__ __forceinline__ void eff_set_base(EffState& E) {
+  E.ib0 = 1.0 / E.base[0];
+  E.ith = 1.0 / E.base[3];
+  E.isq = sqrt(E.ith);
+}
+
 __device__ __forceinline__ void eff_init(EffState& E, const double q[4], bool done) {
   for (int k = 0; k < 4; ++k) E.base[k] = E.p[k] = q[k];
+  eff_set_base(E);
   E.it = 0;
   E.conv = done;
   E.fail = false;
@@ -148,12 +158,13 @@ template <int DIM>
 __device__ __forceinline__ void eff_iterate(const Params& P, const double q[4], const double Mx[5],
                                             const double My[5], EffState& E, double lin_max = kLinMax,
                                             double tol = kEffTol) {
-  const double vs = sqrt(q[3]);
+  // the convergence test scales n by q_n, U by sqrt(q_theta), theta by q_theta
+  const double iq0 = 1.0 / q[0], iq3 = 1.0 / q[3], ivs = sqrt(iq3);
   double* p = E.p;
   double* b = E.base;
   while (!E.conv && !E.fail && !E.reeval) {
     ++E.it;
-    const double ith = 1.0 / b[3];
+    const double ith = E.ith;
     const double w2 = (p[3] - b[3]) * ith * ith;
     double Sx[3], Sy[3] = {1.0, 0.0, 0.0};
     const double w1x = 2.0 * (p[1] - b[1]) * ith;
@@ -165,7 +176,8 @@ __device__ __forceinline__ void eff_iterate(const Params& P, const double q[4], 
       for (int m = 0; m < 3; ++m) Sy[m] = My[m] + w1y * My[m + 1] + w2 * My[m + 2];
     }
     const double pref = (DIM == 1) ? p[0] / sqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
-    const double rx = 1.0 / Sx[0], ry = 1.0 / Sy[0];
+    const double rxy = 1.0 / (Sx[0] * Sy[0]);  // one division for 1/Sx0 and 1/Sy0
+    const double rx = Sy[0] * rxy, ry = Sx[0] * rxy;
     const double mux = Sx[1] * rx, muy = Sy[1] * ry;
     double d[4];
     d[0] = pref * P.dv * Sx[0] * Sy[0];
@@ -179,8 +191,8 @@ __device__ __forceinline__ void eff_iterate(const Params& P, const double q[4], 
     for (int k = 0; k < 4; ++k) {
       const double delta = q[k] - d[k];
       p[k] += delta;
-      const double scale = (k == 0) ? q[0] : (k == 3) ? q[3] : vs;
-      r = fmax(r, fabs(delta) / scale);
+      const double iscale = (k == 0) ? iq0 : (k == 3) ? iq3 : ivs;
+      r = fmax(r, fabs(delta) * iscale);
     }
     if (!(p[0] > 0.0) || !(p[3] > 0.0) || !isfinite(r)) {
       E.fail = true;
@@ -191,10 +203,11 @@ __device__ __forceinline__ void eff_iterate(const Params& P, const double q[4], 
       else E.fail = true;
     }
     if (!E.fail) {
-      const double drift = fmax(fmax(fabs(p[0] - b[0]) / b[0], fabs(p[3] - b[3]) / b[3]),
-                                fmax(fabs(p[1] - b[1]), fabs(p[2] - b[2])) / sqrt(b[3]));
+      const double drift = fmax(fmax(fabs(p[0] - b[0]) * E.ib0, fabs(p[3] - b[3]) * ith),
+                                fmax(fabs(p[1] - b[1]), fabs(p[2] - b[2])) * E.isq);
       if (drift > lin_max) {
         for (int k = 0; k < 4; ++k) b[k] = p[k];
+        eff_set_base(E);
         E.reeval = true;
       }
     }
@@ -203,7 +216,7 @@ __device__ __forceinline__ void eff_iterate(const Params& P, const double q[4], 
 
 // First-order factors that move the Gaussians from E.base to E.p.
 __device__ __forceinline__ void eff_lin(const EffState& E, double& w1x, double& w1y, double& w2) {
-  const double ith = 1.0 / E.base[3];
+  const double ith = E.ith;
   w2 = (E.p[3] - E.base[3]) * ith * ith;
   w1x = 2.0 * (E.p[1] - E.base[1]) * ith;
   w1y = 2.0 * (E.p[2] - E.base[2]) * ith;

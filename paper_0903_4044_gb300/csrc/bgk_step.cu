@@ -90,7 +90,27 @@ __device__ __forceinline__ void stream_cell(const Params& P, const Tables& T,
   double s0 = 0.0, sx = 0.0, sy = 0.0, se = 0.0;
   if (DIM == 2) {
     const ptrdiff_t row = (ptrdiff_t)nx * nv;
-    if (!(bxlo || bxhi || bylo || byhi)) {
+    if (!(bxlo || bxhi || bylo || byhi) && P.nvx == 32) {
+      // interior cell, 32 columns: lane = jx for every j = lane + 32 k, so
+      // sum c_x g = c_x[lane] sum g is taken once after the loop
+#pragma unroll 4
+      for (int j = lane; j < nv; j += 32) {
+        const int vi = T.vinfo[j];
+        const double2 f0 = fc[j];
+        const double2 fx = fc[j - vi_sx(vi) * nv];
+        const double2 fy = fc[j - vi_sy(vi) * row];
+        const double4_32a co = T.coef[j];
+        const double cyj = T.cxy[j].y;
+        double2 ft;
+        ft.x = fma(co.z, fy.x, fma(co.y, fx.x, co.x * f0.x));
+        ft.y = fma(co.z, fy.y, fma(co.y, fx.y, co.x * f0.y));
+        tile[j] = ft;
+        s0 += ft.x;
+        sy = fma(cyj, ft.x, sy);
+        se = fma(co.w, ft.x, se) + ft.y;
+      }
+      sx = T.cx[lane] * s0;
+    } else if (!(bxlo || bxhi || bylo || byhi)) {
       // interior cell: every upwind neighbour is a cell of the grid
 #pragma unroll 4
       for (int j = lane; j < nv; j += 32) {
@@ -227,7 +247,7 @@ __device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, co
   for (int round = 0; round <= kEffMaxIt; ++round) {
     const bool need = round == 0 || E.reeval;
     if (!__any_sync(0xffffffffu, need)) break;
-    const double inv_th = 1.0 / E.base[3];
+    const double inv_th = E.ith;
     double Mt[5];
     axis_sums<L>(T.cx, P.nvx, E.base[1], inv_th, sub, need, px, cons, Mt);
     if (need)
