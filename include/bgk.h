@@ -188,10 +188,7 @@ BGK_API bgk_status bgk_moments(bgk_solver* s, int which, double* mom, int on_dev
  * Synchronises. */
 BGK_API bgk_status bgk_wall_fluxes(bgk_solver* s, int face, double* out, int on_device);
 
-/* Wait for the solver's stream; report a kernel-detected numerical failure
- * (BGK_ERR_NUMERIC) or a bounded in-kernel wait that ran out
- * (BGK_ERR_TIMEOUT: a bulk copy of the pipelined FP32 step that did not
- * complete; the state is then not to be trusted). */
+/* Wait for the solver's stream; report a kernel-detected numerical failure. */
 BGK_API bgk_status bgk_sync(bgk_solver* s);
 
 /* Rankine-Hugoniot states of Eq. (RH) for upstream Mach number mach with the

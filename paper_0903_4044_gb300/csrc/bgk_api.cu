@@ -378,8 +378,6 @@ bgk_status check_flag(bgk_solver* s) {
     return fail(BGK_ERR_NUMERIC, "a cell reached n <= 0, theta <= 0 or a non-finite moment");
   if (h & bgk::ERR_EFFECTIVE)
     return fail(BGK_ERR_NUMERIC, "the effective-parameter iteration did not converge in a cell");
-  if (h & bgk::ERR_TIMEOUT)
-    return fail(BGK_ERR_TIMEOUT, "a bulk copy into shared memory did not complete within its wait limit");
   return BGK_OK;
 }
 
