@@ -187,8 +187,6 @@ class Batch:
         B.bgk_batch_set_persistent(self.h, enable, timeout_s)
         for s in self.solvers:
             s.info = B.bgk_get_info(s.h)
-        for s in self.solvers:
-            s.info = B.bgk_get_info(s.h)
 
     def points(self) -> int:
         return sum(s.ncell * s.nv for s in self.solvers)
