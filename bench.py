@@ -186,6 +186,29 @@ def sizes(w: dict) -> tuple[int, int, int]:
 # --------------------------------------------------------------------------
 # CPU oracle legs (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), with the architecture."""
+    import platform
+    import subprocess
+
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name and os.path.exists("/proc/cpuinfo"):
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+    return f"{name or 'unknown'} ({platform.machine()})"
+
+
 def oracle_sample(w: dict, sample_steps: int):
     """Time `sample_steps` oracle time steps of workload w; returns (updates/s, seconds, threads)."""
     import oracle
@@ -283,7 +306,7 @@ def reference_arm(args, w, rank, pg):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": wname, "sample": label},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{label} per benchmark step"},
+                         "sample": f"{label} per benchmark step", "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -401,7 +424,18 @@ def ours_arm(args, w, world, rank, local, pg):
         sample = max(1, int(3.0e9 // (ncell * nv)))  # about 10 s on 16 host cores
         rate, dt, threads = oracle_sample(w, sample)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{sample} time steps of {w['name']} ({dt:.1f} s)"}
+               "sample": f"{sample} time steps of {w['name']} ({dt:.1f} s)", "cpu_model": cpu_model()}
+        # the same oracle on one core, on a shorter sample (about 5 s)
+        import oracle
+
+        sample1 = max(1, int(1.0e8 // (ncell * nv)))
+        oracle.set_threads(1)
+        try:
+            rate1, dt1, _ = oracle_sample(w, sample1)
+        finally:
+            oracle.set_threads(threads)
+        cpu["single_thread"] = {"value": rate1, "unit": UNIT,
+                                "sample": f"{sample1} time steps of {w['name']} ({dt1:.1f} s)"}
 
     if rank == 0:
         line = {

@@ -106,6 +106,8 @@ def lib():
         L.orc_stream.argtypes = [_C, _D, _D, _D, _D]
         L.orc_relax.argtypes = [_C, _D, _D, _D]
         L.orc_step.argtypes = [_C, _D, _D, ctypes.c_long, _D]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = None
         L.orc_wall_fluxes.argtypes = [_C, _D, _D, ctypes.c_int, _D, _D, _D, _D]
         L.orc_threads.argtypes = []
         L.orc_lid_shear.argtypes = [_C, _D, _D]
@@ -302,6 +304,11 @@ def adjoint_lid_shear(prob: Problem, g, h, nsteps: int):
 
 def threads() -> int:
     return lib().orc_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on."""
+    lib().orc_set_threads(int(n))
 
 
 # --- the two problems of the paper, from raw workload parameters ---------

@@ -83,6 +83,14 @@ int orc_threads(void) {
 #endif
 }
 
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Eq. (Maxw) in normalised units:                                           */
 /*   Phi = n (pi theta)^(-3/2) exp(-|c - U|^2 / theta).                      */

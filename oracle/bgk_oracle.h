@@ -101,6 +101,8 @@ int orc_wall_fluxes(const orc_config* c, const double* g, const double* h, int f
 
 /* Threads used by the OpenMP loops over cells (1 when built without it). */
 int orc_threads(void);
+/* Threads of the OpenMP loops from now on (n > 0). */
+void orc_set_threads(int n);
 
 /* Objective of the adjoint: the lid-integrated shear J = sum over the cells
  * of face YHI of dx * tau_k, tau_k the shear flux of orc_wall_fluxes (the
