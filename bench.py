@@ -468,8 +468,10 @@ def accuracy_arm(args, w):
     torch.cuda.set_device(0)
     ncell, nv, _ = sizes(w)
     xi = W.perturbation(w.get("seed", 0), ncell, nv)
+    # --precision f64 (the default) compares both reduced forms with one FP64 run
+    forms = ["f32", "bf16"] if args.precision == "f64" else [args.precision]
     out = {}
-    for name in ("f64", args.precision):
+    for name in ["f64"] + forms:
         s = solver.make_cavity(w, xi=xi, precision=PRECISION[name])
         t0 = time.perf_counter()
         s.step(w["steps"])
@@ -477,22 +479,24 @@ def accuracy_arm(args, w):
         lid = s.wall_fluxes(B.BGK_FACE_YHI)
         out[name] = (mom, lid, time.perf_counter() - t0)
         s.close()
-    (m64, l64, t64), (mr, lr, tr) = out["f64"], out[args.precision]
+    m64, l64, t64 = out["f64"]
     uw = w["lid_mach"] * (5.0 / 6.0) ** 0.5
-    shear64, shear = float(l64[:, 1].mean()), float(lr[:, 1].mean())
-    line = {
-        "mode": "accuracy", "workload": w["name"], "precision": args.precision, "time_steps": w["steps"],
-        "reference": "FP64 GPU path (oracle parity 1e-12)",
-        "err_n_rel_max": float(np.abs(mr[:, 0] - m64[:, 0]).max() / np.abs(m64[:, 0]).max()),
-        "err_u_over_lid_speed_max": float(np.abs(mr[:, 1:3] - m64[:, 1:3]).max() / uw),
-        "err_theta_rel_max": float(np.abs(mr[:, 3] - m64[:, 3]).max() / np.abs(m64[:, 3]).max()),
-        "err_u_over_lid_speed_rms": float(np.sqrt(((mr[:, 1:3] - m64[:, 1:3]) ** 2).mean()) / uw),
-        "lid_shear_f64": shear64, "lid_shear": shear,
-        "err_lid_shear_rel": abs(shear - shear64) / abs(shear64),
-        "mass_drift_rel": float(abs(mr[:, 0].sum() - m64[:, 0].sum()) / m64[:, 0].sum()),
-        "seconds": {"f64": t64, args.precision: tr},
-    }
-    print(json.dumps(line), flush=True)
+    for name in forms:
+        mr, lr, tr = out[name]
+        shear64, shear = float(l64[:, 1].mean()), float(lr[:, 1].mean())
+        line = {
+            "mode": "accuracy", "workload": w["name"], "precision": name, "time_steps": w["steps"],
+            "reference": "FP64 GPU path (oracle parity 1e-12)",
+            "err_n_rel_max": float(np.abs(mr[:, 0] - m64[:, 0]).max() / np.abs(m64[:, 0]).max()),
+            "err_u_over_lid_speed_max": float(np.abs(mr[:, 1:3] - m64[:, 1:3]).max() / uw),
+            "err_theta_rel_max": float(np.abs(mr[:, 3] - m64[:, 3]).max() / np.abs(m64[:, 3]).max()),
+            "err_u_over_lid_speed_rms": float(np.sqrt(((mr[:, 1:3] - m64[:, 1:3]) ** 2).mean()) / uw),
+            "lid_shear_f64": shear64, "lid_shear": shear,
+            "err_lid_shear_rel": abs(shear - shear64) / abs(shear64),
+            "mass_drift_rel": float(abs(mr[:, 0].sum() - m64[:, 0].sum()) / m64[:, 0].sum()),
+            "seconds": {"f64": t64, name: tr},
+        }
+        print(json.dumps(line), flush=True)
 
 
 def batch_arm(args, world, rank, local, pg):
@@ -789,7 +793,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--tile", type=int, default=0, help="cells per CTA of the step kernel (0 = library choice)")
     ap.add_argument("--accuracy", action="store_true",
-                    help="report per-field errors of --precision against the FP64 path instead of timing")
+                    help="report per-field errors of --precision (both reduced forms when f64) against the FP64 path instead of timing")
     ap.add_argument("--precision", default="f64", choices=sorted(PRECISION),
                     help="state storage: f64, f32, or bf16 deviation from the absolute Maxwellian")
     ap.add_argument("--checkpoint-every", type=int, default=100, help="adjoint workload: steps per checkpoint")
