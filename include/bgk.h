@@ -107,7 +107,11 @@ typedef struct {
   int32_t precision;    /* bgk_precision */
   int32_t tile_cells;   /* spatial cells per CTA of the step kernel: 0 = chosen
                            by the library, else 1, 2, 4 or 8 (tuning knob; the
-                           results do not depend on it) */
+                           results do not depend on it beyond the rounding
+                           order of reduced-precision sums; for 2D FP32 and
+                           BF16 states, 1 runs the pipelined one-cell kernel
+                           when its buffers fit, with the one-cell block's
+                           results) */
   int32_t reserved0;    /* must be 0 */
   double x0, lx;        /* domain [x0, x0 + lx] */
   double y0, ly;        /* domain [y0, y0 + ly] (dim 2) */
