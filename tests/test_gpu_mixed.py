@@ -10,8 +10,7 @@ most 2^-7 |d|; the initial rounding plus one stored step stay within
 1.2e-2 max|d| + 2e-6 max|f|.  Macroscopic fields
 after a run average those roundings over every velocity of a cell: the
 bounds used below (FP32 2e-5, BF16 2e-3, velocities relative to the lid
-speed) were set from the measured errors with a margin of about 10 and are
-stated in the design doc with the measured values.
+speed) were set from the measured errors with a margin of about 10.
 """
 import numpy as np
 import pytest
