@@ -46,8 +46,9 @@ DETAIL = {"f64": "FP64 state and arithmetic",
 
 # DRAM bytes per launch of the step kernel from an ncu capture (dram__bytes_
 # read.sum + write.sum), valid only for the kernel sources that were
-# captured: the SHA-1 of those files must match, else traffic is reported as
-# null.  Captures and commands: profiles/step_f64_cavity64.md.
+# captured and for the kernel that is launched: the SHA-1 of those files
+# and the kernel name must match, else traffic is reported as null.  The
+# capture commands sit with the ncu summaries under profiles/.
 MEASURED_TRAFFIC = {
     ("cavity_kn0.1_ma0.1_64x64_v32x32_f64", "f64"): {
         "bytes": 169.0e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
