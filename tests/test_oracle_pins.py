@@ -372,6 +372,108 @@ def test_wall_flux_equilibrium_pressure(orc):
         np.testing.assert_allclose(mass, 0.0, atol=1e-15)
 
 
+_NC, _THC, _UW, _THW = 1.3, 0.8, 0.37, 1.45   # gas density, temperature; wall speed, temperature
+
+
+def _moving_wall_fluxes(orc, face, nn, h_factor=None, thw=_THW):
+    """orc_wall_fluxes (and orc_lid_shear on the lid face) for a resting
+    Maxwellian gas (n_c, theta_c), written here from Eq. (Maxw) reduced to two
+    velocity components, G = n/(pi theta) exp(-|c|^2/theta) and H = theta G/2
+    unless ``h_factor`` replaces theta/2, against a diffuse wall of ``face``
+    moving tangentially at U_W with temperature theta_W.  The velocity box is
+    [-10, 10]^2 (Gaussian tails below 1e-40), with ``nn`` nodes along the
+    wall normal and 64 along the tangent; 3 x 3 identical cells."""
+    xface = face in (orc.XLO, orc.XHI)
+    nvx, nvy = (nn, 64) if xface else (64, nn)
+    wall = (1.0, 0.0, _UW, thw) if xface else (1.0, _UW, 0.0, thw)
+    states = [(1.0, 0.0, 0.0, 1.0)] * 4
+    states[face] = wall
+    c = orc.make_config(dim=2, nx=3, ny=3, lx=1.5, ly=1.5, nvx=nvx, nvy=nvy, vx=(-10, 10),
+                        vy=(-10, 10), dt=1e-3, bc_kind=(1,) * 4, bc_state=tuple(states))
+    prob = orc.Problem(c)
+    cx, cy = orc.velocities(c)
+    G = _NC / (math.pi * _THC) * np.exp(-(cx ** 2 + cy ** 2) / _THC)
+    H = (0.5 * _THC if h_factor is None else h_factor) * G
+    g, h = np.tile(G, (prob.ncell, 1)), np.tile(H, (prob.ncell, 1))
+    out = np.array(orc.wall_fluxes(prob, g, h, face))   # (mass, shear, normal, energy) x 3 face cells
+    J = orc.lid_shear(prob, g, h) if face == orc.YHI else None
+    return out, J
+
+
+@pytest.mark.parametrize("face", [0, 1, 2, 3])
+def test_wall_fluxes_moving_hot_wall_closed_form(orc, face):
+    # Pins orc_wall_fluxes (mass, shear, normal momentum, energy) and
+    # orc_lid_shear with non-zero closed forms: the zero-net-mass-flux diffuse
+    # wall below Eq. (bc_cavity), moving tangentially at U_W with temperature
+    # theta_W, facing a resting Maxwellian gas (n_c, theta_c).
+    #
+    # Per unit density, a resting reduced Maxwellian at temperature theta
+    # carries, over the half-space of velocities moving one way along the
+    # normal (1D half-range Gaussian integrals, the tangential factor being 1):
+    #   int |c_n| G           = sqrt(theta) / (2 sqrt(pi))       (particle flux)
+    #   int c_n^2 G           = theta / 4                        (half the pressure)
+    #   int |c_n| c_n^2 G     = theta^(3/2) / (2 sqrt(pi))
+    # and over the full tangential line int c_t G = U_t, int c_t^2 G = theta/2 + U_t^2;
+    # the Chu function H = theta G / 2 adds theta/2 per particle to |c|^2.
+    # Incident particle flux: Gamma = n_c sqrt(theta_c) / (2 sqrt(pi)).  The
+    # wall density n_W makes the emitted flux equal it, so
+    #   n_W = n_c sqrt(theta_c / theta_W),
+    #   mass   = 0,
+    #   shear  = sum c_t c_n F dV = U_W Gamma   (only emitted particles carry c_t),
+    #   normal = sum c_n^2 F dV = (n_c theta_c + n_W theta_W) / 4,
+    #   energy = sum c_n (|c|^2 g + h) dV
+    #          = Gamma [theta_W + theta_W/2 + U_W^2 + theta_W/2]        (emitted)
+    #          - Gamma [theta_c + theta_c/2 + theta_c/2]                 (incident)
+    #          = Gamma (2 theta_W - 2 theta_c + U_W^2),
+    #   lid shear J = L_x * shear (on the lid face).
+    # The oracle's half-range sums are midpoint rules on [0, 10] whose error
+    # expands in even powers of the node spacing (Euler-Maclaurin; the cut at
+    # c_n = 0 falls on a cell edge), so three spacings extrapolated by
+    # Richardson leave an O(h^6) error, measured at 3e-12 of the largest flux.
+    F = {nn: _moving_wall_fluxes(orc, face, nn) for nn in (400, 800, 1600)}
+    r1 = (4 * F[800][0] - F[400][0]) / 3
+    r2 = (4 * F[1600][0] - F[800][0]) / 3
+    ext = (16 * r2 - r1) / 15
+    gam = _NC * math.sqrt(_THC) / (2 * math.sqrt(math.pi))
+    closed = np.array([0.0, _UW * gam, _NC * (_THC + math.sqrt(_THC * _THW)) / 4,
+                       gam * (2 * _THW - 2 * _THC + _UW ** 2)])
+    scale = np.abs(closed).max()
+    for k in range(4):
+        np.testing.assert_allclose(ext[k], closed[k], rtol=0, atol=1e-11 * scale)
+    # mass is zero exactly at every spacing, not only in the limit
+    np.testing.assert_allclose(F[400][0][0], 0.0, atol=1e-14 * scale)
+    if face == orc.YHI:
+        Js = {nn: F[nn][1] for nn in F}
+        j1 = (4 * Js[800] - Js[400]) / 3
+        j2 = (4 * Js[1600] - Js[800]) / 3
+        assert (16 * j2 - j1) / 15 == pytest.approx(1.5 * _UW * gam, rel=1e-11)
+
+
+@pytest.mark.parametrize("face", [0, 3])
+def test_wall_fluxes_exact_discrete_relations(orc, face):
+    # Pins the same function at one spacing (64 nodes over [-10, 10]), where
+    # the half-range sums are still about 1e-2 from their limits, through
+    # relations that hold for the discrete sums exactly: at this spacing the
+    # full-line sums of a Gaussian (the tangential factors, and the normal
+    # pressure below) converge spectrally, to below 1e-30.
+    # (1) Only incident particles carry the gas's h, with weight c_n < 0, so
+    #     the energy flux changes by -(k1 - k0) Gamma_d when h = k G replaces
+    #     h = k0 G; and the shear is U_W Gamma_d with the same discrete
+    #     incident particle flux Gamma_d.  Hence
+    #     (e(k1) - e(k0)) / shear = -(k1 - k0) / U_W.
+    # (2) With theta_W = theta_c the half-range sums of both halves coincide,
+    #     n_W = n_c, and energy = U_W^2 Gamma_d = U_W * shear, while the normal
+    #     flux is the full-range pressure n_c theta_c / 2.
+    out0, _ = _moving_wall_fluxes(orc, face, 64, h_factor=0.0)
+    out1, _ = _moving_wall_fluxes(orc, face, 64, h_factor=0.7)
+    shear = out0[1]
+    np.testing.assert_allclose((out1[3] - out0[3]) / shear, -0.7 / _UW, rtol=1e-12)
+    np.testing.assert_allclose(out1[1], shear, rtol=1e-14)
+    iso, _ = _moving_wall_fluxes(orc, face, 64, thw=_THC)
+    np.testing.assert_allclose(iso[3], _UW * iso[1], rtol=1e-12)
+    np.testing.assert_allclose(iso[2], _NC * _THC / 2, rtol=1e-12)
+
+
 # --------------------------------------------------------------------------
 # Whole steps: invariants of the two problems of the paper
 # --------------------------------------------------------------------------
