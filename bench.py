@@ -40,8 +40,11 @@ BYTES_PER_UPDATE = {"f64": 32.0, "f32": 16.0, "bf16": 8.0}
 PRECISION = {"f64": 0, "f32": 1, "bf16": 2}
 DTYPE = {"f64": "f64", "f32": "f32", "bf16": "bf16"}
 DETAIL = {"f64": "FP64 state and arithmetic",
-          "f32": "FP32 state and streaming/relaxation; float-float moment sums finished in FP64; FP64 per-cell parameters",
-          "bf16": "BF16 deviation from the absolute Maxwellian; FP32 arithmetic; float-float moment sums finished in FP64; FP64 per-cell parameters"}
+          "f32": ("FP32 state and arithmetic; moment sums carried in float-float (about 48 bits) and rounded "
+                  "once to FP32 per cell; FP32 effective parameters; normalisation in float-float rounded to FP32"),
+          "bf16": ("BF16 deviation from the absolute Maxwellian (FP32 arithmetic, stochastic rounding on store); "
+                   "moment sums in float-float rounded once to FP32 per cell; FP32 effective parameters; "
+                   "normalisation in float-float rounded to FP32")}
 
 
 # DRAM bytes per launch of the step kernel from an ncu capture (dram__bytes_

@@ -76,8 +76,12 @@ typedef enum {
 
 typedef enum {
   BGK_F64 = 0,     /* state stored and computed in FP64 */
-  BGK_F32 = 1,     /* state stored in FP32, moments accumulated in FP64 */
-  BGK_BF16_DEV = 2 /* state stored as BF16 deviation from a fixed Maxwellian */
+  BGK_F32 = 1,     /* state stored and computed in FP32; per-cell moment sums
+                      carried in float-float (about 48 bits), rounded once to
+                      FP32 for the step and finished in FP64 by bgk_moments */
+  BGK_BF16_DEV = 2 /* state stored as BF16 deviation from the absolute
+                      Maxwellian (n = 1, U = 0, theta = 1), computed as for
+                      BGK_F32 */
 } bgk_precision;
 
 typedef enum {
@@ -350,16 +354,20 @@ BGK_API bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int chec
  *
  *   cfg     as for bgk_create (validated the same way; tile_cells honoured);
  *           the work goes to cfg->cuda_stream
- *   f_in    device pointer, state at time level n (STATE LAYOUT), read only
+ *   f_in    device pointer, state at time level n (STATE LAYOUT), read
+ *           only, 16-byte aligned
  *   f_out   device pointer, state at level n+1 (same size, must not overlap
- *           f_in)
- *   mom_out device pointer, ncell*4 doubles: moments (n, ux, uy, theta) of
- *           the post-streaming state, as bgk_moments(which = 1)
+ *           f_in), 16-byte aligned
+ *   mom_out device pointer, ncell*4 doubles, 32-byte aligned: moments
+ *           (n, ux, uy, theta) of the post-streaming state, as
+ *           bgk_moments(which = 1)
+ * The library cannot see the buffers' sizes: the caller guarantees them.
+ * A misaligned pointer gets BGK_ERR_INVALID_ARG before any GPU work.
  * The result equals bgk_set_state(f_in) + bgk_step(1) on a solver made from
  * cfg.  The call synchronises cfg->cuda_stream before returning and reports
  * BGK_ERR_NUMERIC like bgk_sync.  The first call on a device looks up the
- * scratch array's device address for that device (make that first call
- * before any stream capture).  All calls share the one scratch array and it
+ * scratch array's device address for that device; make that first call
+ * before any stream capture begins.  All calls share the one scratch array and it
  * keeps the last call's contents (the error flag is cleared and the tables
  * rebuilt on every call): calls whose work overlaps on the GPU, from several
  * threads or streams, race and must be serialised by the caller. */

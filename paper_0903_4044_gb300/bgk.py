@@ -259,6 +259,12 @@ def bgk_step_noalloc(cfg: bgk_config, f_in, f_out, mom_out) -> None:
     m, dm = _ptr(mom_out)
     if not (da and db and dm):
         raise ValueError("bgk_step_noalloc takes device buffers only")
+    # the C call cannot see buffer sizes: check them here
+    ncell = cfg.nx * (cfg.ny if cfg.dim == 2 else 1)
+    nv = cfg.nvx * (cfg.nvy if cfg.dim == 2 else 1)
+    if not (f_in.numel() == f_out.numel() == ncell * nv * 2 and mom_out.numel() >= ncell * 4):
+        raise ValueError(f"bgk_step_noalloc: f_in and f_out need {ncell * nv * 2} doubles, "
+                         f"mom_out at least {ncell * 4}")
     _check(lib().bgk_step_noalloc(ctypes.byref(cfg), a, b, m), "bgk_step_noalloc")
 
 

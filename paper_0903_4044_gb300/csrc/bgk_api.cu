@@ -802,6 +802,11 @@ extern "C" bgk_status bgk_step_noalloc(const bgk_config* cfg, const double* f_in
   if (st != BGK_OK) return st;
   if (cfg->precision != BGK_F64)
     return fail(BGK_ERR_UNSUPPORTED, "bgk_step_noalloc takes BGK_F64 states only");
+  // the step kernel moves (g, h) pairs as 16-byte vectors and writes each
+  // cell's moments with one 32-byte store
+  if ((uintptr_t)f_in % 16 || (uintptr_t)f_out % 16 || (uintptr_t)mom_out % 32)
+    return fail(BGK_ERR_INVALID_ARG, "bgk_step_noalloc: f_in and f_out must be 16-byte aligned, "
+                "mom_out 32-byte aligned");
   const size_t elems = (size_t)P.nx * P.ny * P.nv;
   const char *a = (const char*)f_in, *b = (const char*)f_out;
   if (a < b + elems * sizeof(double2) && b < a + elems * sizeof(double2))

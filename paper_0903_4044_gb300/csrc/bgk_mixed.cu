@@ -1,10 +1,14 @@
 // bgk_mixed.cu - the reduced-precision BGK step (2D): the state is stored as
 // FP32 (g, h) pairs, or as BF16 deviations (dg, dh) from the absolute
 // Maxwellian M_abs (n = 1, U = 0, theta = 1), and streamed and relaxed on the
-// FP32 pipe; moment sums are carried in FP32 pairs by error-free
-// transformations (Kahan per lane, TwoSum across lanes) and finished in FP64;
-// the per-cell parameters (moments, nu, effective Maxwellian, normalisation)
-// are FP64 with cells in lanes; the Gaussian factors are FP32.
+// FP32 pipe.  Moment sums are carried as float-float pairs by error-free
+// transformations (Kahan per lane, TwoSum across lanes: about 48 significant
+// bits); the pairs are published per cell, and bgk_moments finishes them in
+// FP64 on request, while the step itself rounds each sum once to FP32 and
+// forms n, U, theta, nu and the relaxation weight in FP32.  The effective
+// Maxwellian parameters are two FP32 updates; its normalisation a n/(pi
+// theta) is evaluated in float-float and rounded once to FP32; the Gaussian
+// factors are FP32.
 //
 // Conservation in low precision: streaming uses the flux form
 // f~ = f - ax (f - f_upx) - ay (f - f_upy), which telescopes whatever the

@@ -74,6 +74,48 @@ def test_noalloc_shock_matches_solver_step():
     s.close()
 
 
+def test_noalloc_honours_tile_and_stream():
+    # tile_cells = 2 and a non-default stream: the same results as the solver
+    # path built from the same configuration
+    import torch
+
+    w = W.scaled(W.CAVITY_64, n=18, nv=16)
+    xi = W.perturbation(3, 18 * 18, 16 * 16)
+    st = torch.cuda.Stream()
+    cfg = solver.cavity_config(**w, tile_cells=2, stream=st.cuda_stream)
+    s = solver.Solver(cfg)
+    s.init_uniform((1.0, 0.0, 0.0, 1.0), xi, 1e-3)
+    assert s.info.tile_cells == 2
+    _two_calls(s, cfg)
+    s.close()
+
+
+def test_noalloc_rejects_misaligned_and_short_buffers():
+    # both checks run before any GPU work: a float64 view at an 8-byte offset
+    # gets BGK_ERR_INVALID_ARG from the library, a buffer of the wrong size a
+    # ValueError from the binding
+    import torch
+
+    w = W.scaled(W.CAVITY_64, n=4, nv=8)
+    cfg = solver.cavity_config(**w)
+    n = 16 * 64 * 2
+    base = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    good = torch.zeros(n, dtype=torch.float64, device="cuda")
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    m = torch.empty(16 * 4, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.BgkError) as e:
+        B.bgk_step_noalloc(cfg, base[1:], out, m)
+    assert e.value.status == B.BGK_ERR_INVALID_ARG
+    mbase = torch.empty(16 * 4 + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.BgkError) as e:
+        B.bgk_step_noalloc(cfg, good, out, mbase[1:])
+    assert e.value.status == B.BGK_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        B.bgk_step_noalloc(cfg, good[:-2], out, m)
+    with pytest.raises(ValueError):
+        B.bgk_step_noalloc(cfg, good, out, m[:-1])
+
+
 def test_noalloc_refuses_tables_beyond_its_scratch():
     import torch
 
