@@ -175,10 +175,58 @@ def workload(name: str) -> dict:
     if name in ("shock", W.SHOCK_M2["name"]):
         return W.SHOCK_M2
     if name in ("cavity256_f64", "cavity256"):
-        return W.scaled(W.CAVITY_256, steps=200, name="cavity_kn0.05_ma0.05_256x256_v48x48_200steps")
+        return W.scaled(W.CAVITY_256, steps=200, name=CAVITY256_200)
     if name == "cavity256_full":
         return W.CAVITY_256
     raise SystemExit(f"unknown workload {name}")
+
+
+CAVITY256_200 = "cavity_kn0.05_ma0.05_256x256_v48x48_200steps"
+
+
+def bench_config(w: dict, precision: str, world: int) -> dict:
+    """The `config` object of a single-workload line (both arms print the same one)."""
+    ncell, nv, _ = sizes(w)
+    state_gb = BYTES_PER_UPDATE[precision] / 2 * ncell * nv / 1e9
+    return {"workload": w["name"], "cells": ncell, "velocities": nv, "time_steps": w["steps"],
+            "precision": precision, "arithmetic": DETAIL[precision], "parallelism": f"replica x{world}",
+            "l2": (f"state {state_gb:.2f} GB per buffer; L2 flushed (256 MB write) between timed GPU steps")}
+
+
+BATCH_NAME = "batch_64_cavities_16_shocks_seed0"
+
+
+def batch_points(ws) -> int:
+    return sum(w["n"] ** 2 * w["nv"] ** 2 if w["kind"] == "cavity" else w["nx"] * w["nvx"] for w in ws)
+
+
+def config_for(args, w, world: int) -> dict:
+    """The `config` object of a line; the GPU arm and the reference arm print the same one."""
+    from paper_0903_4044_gb300 import workloads as W
+
+    if args.workload == "batch":
+        ws = W.batch_instances(0)
+        return {"workload": BATCH_NAME, "instances": len(ws), "points": batch_points(ws),
+                "time_steps": args.time_steps or 20, "precision": "f32",
+                "launch": ("one persistent cooperative kernel per benchmark step (grid barrier between time "
+                           "steps), captured in a CUDA graph") if args.persistent else
+                          "one CUDA graph per benchmark step, one branch of step kernels per instance",
+                "parallelism": f"replica x{world}",
+                "l2": "inputs larger than L2 (9.4 GB of FP32 state)"}
+    if args.workload == "adjoint":
+        ncell, nv, _ = sizes(w)
+        return {"workload": f"adjoint_{w['name']}", "cells": ncell, "velocities": nv, "time_steps": w["steps"],
+                "checkpoint_every": args.checkpoint_every, "objective": "lid-integrated shear",
+                "gradients": "Kn, lid speed, every entry of f0",
+                "update": "one (cell, velocity) point of one differentiated time step",
+                "precision": "f64", "parallelism": f"replica x{world}",
+                "l2": "inputs larger than L2 (268 MB state, 27 GB of segment states)"}
+    if args.workload in ("shock3v", "shock3v_m15"):
+        ncell, nv = w["nx"], w["nv"][0] * w["nv"][1] * w["nv"][2]
+        return {"workload": w["name"], "cells": ncell, "velocities": nv, "time_steps": w["steps"],
+                "precision": "f64", "parallelism": f"replica x{world}",
+                "l2": "flushed (256 MB write) between timed GPU steps; state larger than L2"}
+    return bench_config(w, args.precision, world)
 
 
 def sizes(w: dict) -> tuple[int, int, int]:
@@ -308,7 +356,7 @@ def reference_arm(args, w, rank, pg):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": wname, "sample": label},
+        "data": "synthetic", "config": config_for(args, w, args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{label} per benchmark step", "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -319,20 +367,55 @@ def reference_arm(args, w, rank, pg):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
-def ours_arm(args, w, world, rank, local, pg):
+def kernel_name(precision: str, dim: int, tile: int) -> str:
+    if precision == "f64":
+        return "bgk::step_f64_kernel"
+    if dim == 1:
+        return "bgk::step_mixed1d_kernel"
+    # tile 1 of the 2D reduced-precision step is the pipelined kernel
+    return "bgk::step_mixed_pipe_kernel" if tile == 1 else "bgk::step_mixed_kernel"
+
+
+def roofline(w: dict, precision: str, per_launch: float, kname: str, traffic_override=None) -> dict:
+    """Roofline of the step kernel from its CUDA-event launch time: FP64 forms
+    against the nominal FP64 rate when that binds, else against measured HBM."""
+    ncell, nv, dim = sizes(w)
+    peaks = load_peaks()
+    bytes_launch = BYTES_PER_UPDATE[precision] * ncell * nv
+    flops_launch = FLOPS_PER_UPDATE[dim] * ncell * nv if precision == "f64" else 0.0
+    hbm_achieved = bytes_launch / per_launch / 1e9
+    alu_achieved = flops_launch / per_launch / 1e12
+    t_hbm = bytes_launch / (peaks["hbm_gbs"] * 1e9)
+    t_alu = flops_launch / FP64_NOMINAL_FLOPS
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": alu_achieved, "peak": FP64_NOMINAL_FLOPS / 1e12,
+                "unit": "TFLOP/s", "frac": alu_achieved / (FP64_NOMINAL_FLOPS / 1e12),
+                "peak_source": "nominal FP64 (unit counts x clock)"}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peaks["source"]}
+    traffic = traffic_override if traffic_override is not None else measured_traffic(w["name"], precision, kname)
+    roof.update({"traffic": traffic, "kernel": kname, "launch_ms": per_launch * 1e3,
+                 "bytes_per_update": BYTES_PER_UPDATE[precision], "hbm_gbs": hbm_achieved,
+                 "hbm_frac": hbm_achieved / peaks["hbm_gbs"]})
+    if precision == "f64":
+        roof.update({"flops_per_update": FLOPS_PER_UPDATE[dim], "fp64_tflops": alu_achieved,
+                     "fp64_frac": alu_achieved / (FP64_NOMINAL_FLOPS / 1e12)})
+    return roof
+
+
+def time_single(args, w, precision, world, local, pg, stream, e2e=True):
+    """Device-timed and end-to-end rates of one solver on workload w.
+    Returns (value, elapsed_s, per_launch_s, e2e_dict, tile, launches)."""
     import torch
 
     from paper_0903_4044_gb300 import bgk as B
-    from paper_0903_4044_gb300 import build, solver
+    from paper_0903_4044_gb300 import solver
     from paper_0903_4044_gb300 import workloads as W
 
-    torch.cuda.set_device(local)
-    build.build()
-    stream = torch.cuda.current_stream()
     ncell, nv, dim = sizes(w)
     nsteps = w["steps"]
-
-    prec = PRECISION[args.precision]
+    prec = PRECISION[precision]
     if w["kind"] == "shock":
         s = solver.make_shock(w, stream=stream.cuda_stream, tile_cells=args.tile, precision=prec)
     else:
@@ -356,23 +439,20 @@ def ours_arm(args, w, world, rank, local, pg):
         flush.zero_()
         one_step()
     torch.cuda.synchronize()
-
     pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
              for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier(pg)
-        torch.cuda.synchronize()
-        t_start.record(stream)
-        for k in range(args.steps):
-            flush.zero_()           # L2 flush between timed steps (256 MB write)
-            one_step(pairs[k])
-        t_end.record(stream)
-        torch.cuda.synchronize()
-        barrier(pg)
+    barrier(pg)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(args.steps):
+        flush.zero_()           # L2 flush between timed steps (256 MB write)
+        one_step(pairs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
     B.bgk_sync(s.h)
-    elapsed = t_start.elapsed_time(t_end) / 1e3
-    elapsed = max_over_ranks(pg, elapsed)
+    elapsed = max_over_ranks(pg, t_start.elapsed_time(t_end) / 1e3)
     kernel_s = sum(a.elapsed_time(b) for a, b in pairs) / 1e3
     launches = args.steps * nsteps
     per_launch = kernel_s / launches
@@ -384,8 +464,8 @@ def ours_arm(args, w, world, rank, local, pg):
         B.bgk_set_state(s.h, f0_host.numpy())       # H2D, synchronous on the source
         B.bgk_step(s.h, nsteps)
         B.bgk_moments(s.h, mom_host.numpy(), 0)     # D2H, synchronises
-    e2e = None
-    if not args.no_e2e:
+    e2e_out = None
+    if e2e and not args.no_e2e:
         for _ in range(args.warmup):
             e2e_step()
         barrier(pg)
@@ -394,34 +474,122 @@ def ours_arm(args, w, world, rank, local, pg):
             e2e_step()
         e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
         barrier(pg)
-        e2e = {"value": world * updates / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": int(f0_host.numel() * 8),
-               "d2h_bytes_per_step": int(mom_host.numel() * 8)}
+        e2e_out = {"value": world * updates / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": int(f0_host.numel() * 8),
+                   "d2h_bytes_per_step": int(mom_host.numel() * 8)}
+    tile = int(s.info.tile_cells)
+    s.close()
+    del flush, f0_dev
+    torch.cuda.empty_cache()
+    return value, elapsed, per_launch, e2e_out, tile, launches
 
-    peaks = load_peaks()
-    bytes_launch = BYTES_PER_UPDATE[args.precision] * ncell * nv
-    flops_launch = FLOPS_PER_UPDATE[dim] * ncell * nv if args.precision == "f64" else 0.0
-    hbm_achieved = bytes_launch / per_launch / 1e9
-    alu_achieved = flops_launch / per_launch / 1e12
-    t_hbm = bytes_launch / (peaks["hbm_gbs"] * 1e9)
-    t_alu = flops_launch / FP64_NOMINAL_FLOPS
-    if t_alu >= t_hbm:
-        roof = {"bound": "alu", "achieved": alu_achieved, "peak": FP64_NOMINAL_FLOPS / 1e12,
-                "unit": "TFLOP/s", "frac": alu_achieved / (FP64_NOMINAL_FLOPS / 1e12),
-                "peak_source": "nominal FP64 (unit counts x clock)"}
-    else:
-        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peaks["source"]}
-    if args.precision == "f64":
-        kname = "bgk::step_f64_kernel"
-    elif dim == 1:
-        kname = "bgk::step_mixed1d_kernel"
-    else:  # tile 1 of the 2D reduced-precision step is the pipelined kernel
-        kname = "bgk::step_mixed_pipe_kernel" if int(s.info.tile_cells) == 1 else "bgk::step_mixed_kernel"
-    traffic = args.traffic if args.traffic is not None else measured_traffic(w["name"], args.precision, kname)
-    roof.update({"traffic": traffic, "kernel": kname,
-                 "launch_ms": per_launch * 1e3, "hbm_gbs": hbm_achieved,
-                 "hbm_frac": hbm_achieved / peaks["hbm_gbs"], "fp64_tflops": alu_achieved})
+
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def load_cavity256_golden():
+    """The oracle's stored fields after a prefix of the 256^2 x 48^2 cavity run
+    (written by tests/golden/gen_cavity256.py): (steps, sampled moments rows,
+    lid rows, J, mass), or None when no file is present."""
+    import glob
+    import re
+
+    files = sorted(glob.glob(os.path.join(GOLDEN_DIR, "cavity256_*steps_moments.txt")))
+    if not files:
+        return None
+    f = files[-1]
+    steps = int(re.search(r"cavity256_(\d+)steps_moments", f).group(1))
+    mom = np.loadtxt(f)
+    lidf = f.replace("_moments.txt", "_lid.txt")
+    J = mass = None
+    with open(lidf) as fh:
+        for line in fh:
+            if line.startswith("# J "):
+                J = float(line.split()[2])
+            if line.startswith("# mass "):
+                mass = float(line.split()[2])
+    return steps, mom, np.loadtxt(lidf), J, mass
+
+
+def oracle_errors(forms, local):
+    """Per-field errors of each form after the stored prefix of the 256^2 x 48^2
+    cavity run, against the oracle's stored fields (sampled cells and the lid)."""
+    from paper_0903_4044_gb300 import bgk as B
+    from paper_0903_4044_gb300 import solver
+    from paper_0903_4044_gb300 import workloads as W
+
+    g = load_cavity256_golden()
+    if g is None:
+        return None
+    steps, rows, lid, J, mass = g
+    w = W.CAVITY_256
+    n = w["n"]
+    ix, iy = rows[:, 0].astype(int), rows[:, 1].astype(int)
+    want = rows[:, 2:6]
+    uw = w["lid_mach"] * (5.0 / 6.0) ** 0.5
+    xi = W.perturbation(w["seed"], n * n, w["nv"] * w["nv"])
+    out = {"time_steps": steps, "reference": f"oracle fields after {steps} steps "
+           f"(tests/golden/cavity256_{steps}steps_*.txt; {len(rows)} sampled cells, every lid cell)"}
+    for name in forms:
+        s = solver.make_cavity(w, xi=xi, precision=PRECISION[name])
+        t0 = time.perf_counter()
+        s.step(steps)
+        mom = s.moments().reshape(n, n, 4)
+        fl = s.wall_fluxes(B.BGK_FACE_YHI)
+        secs = time.perf_counter() - t0
+        dx = s.info.dx
+        s.close()
+        got = mom[iy, ix]
+        Jg = float(dx * fl[:, 1].sum())
+        massg = float(mom[:, :, 0].sum() * dx * dx)
+        out[name] = {
+            "err_n_rel_max": float(np.abs(got[:, 0] - want[:, 0]).max() / np.abs(want[:, 0]).max()),
+            "err_u_over_lid_speed_max": float(np.abs(got[:, 1:3] - want[:, 1:3]).max() / uw),
+            "err_u_over_lid_speed_rms": float(np.sqrt(((got[:, 1:3] - want[:, 1:3]) ** 2).mean()) / uw),
+            "err_theta_rel_max": float(np.abs(got[:, 3] - want[:, 3]).max() / np.abs(want[:, 3]).max()),
+            "err_lid_shear_cell_rel_max": float(np.abs(fl[:, 1] - lid[:, 2]).max() / np.abs(lid[:, 2]).max()),
+            "err_lid_shear_J_rel": abs(Jg - J) / abs(J),
+            "err_mass_rel": abs(massg - mass) / mass,
+            "seconds": secs,
+        }
+    return out
+
+
+def ours_arm(args, w, world, rank, local, pg):
+    import torch
+
+    from paper_0903_4044_gb300 import build
+
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    ncell, nv, dim = sizes(w)
+    nsteps = w["steps"]
+
+    with ClockSampler(local) as clk:
+        value, elapsed, per_launch, e2e, tile, launches = time_single(args, w, args.precision, world, local,
+                                                                      pg, stream)
+        kname = kernel_name(args.precision, dim, tile)
+        roof = roofline(w, args.precision, per_launch, kname, args.traffic)
+        # the reduced-precision forms of the same workload, timed the same way
+        forms = None
+        if w["name"] == CAVITY256_200 and args.precision == "f64" and not args.no_forms:
+            forms = {}
+            for name in ("f32", "bf16"):
+                v, el, pl, e2, t, ln = time_single(args, w, name, world, local, pg, stream)
+                forms[name] = {"value": v, "unit": UNIT, "ms_per_step": 1e3 * el / args.steps,
+                               "tile_cells": t, "arithmetic": DETAIL[name],
+                               "roofline": roofline(w, name, pl, kernel_name(name, dim, t)), "e2e": e2, "gpu_launches": ln,
+                               "speedup_vs_f64": v / value}
+                launches += ln
+    clocks = clk.summary()
+    if forms is not None and rank == 0:
+        errs = oracle_errors(["f64", "f32", "bf16"], local)
+        if errs is not None:
+            forms["f64"] = {"err_vs_oracle": errs["f64"]}
+            for name in ("f32", "bf16"):
+                forms[name]["err_vs_oracle"] = errs[name]
+            forms["err_reference"] = {k: errs[k] for k in ("time_steps", "reference")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -446,22 +614,23 @@ def ours_arm(args, w, world, rank, local, pg):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": w["name"], "cells": ncell, "velocities": nv, "time_steps": nsteps,
-                       "tile_cells": int(s.info.tile_cells),
-                       "precision": args.precision, "arithmetic": DETAIL[args.precision],
-                       "parallelism": f"replica x{world}",
-                       "l2": "flushed (256 MB write) between timed steps"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "config": config_for(args, w, world),
+            "tile_cells": tile,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches,
         }
+        if forms is not None:
+            line["forms"] = forms
         print(json.dumps(line), flush=True)
-    s.close()
 
 
 def accuracy_arm(args, w):
     """Per-field error of a reduced-precision run against the FP64 GPU path
-    (which matches the CPU oracle to 1e-12 on every configuration the oracle
-    can finish): n, U, theta of every cell and the lid's mean shear flux."""
+    over the whole run (20000 steps of the 256^2 cavity are beyond the
+    oracle's reach on the host; the FP64 path itself is compared with the
+    oracle's stored fields after a prefix of that run by the GPU tests and by
+    the `forms` of the default benchmark): n, U, theta of every cell and the
+    lid's mean shear flux."""
     import torch
 
     from paper_0903_4044_gb300 import bgk as B
@@ -490,7 +659,7 @@ def accuracy_arm(args, w):
         shear64, shear = float(l64[:, 1].mean()), float(lr[:, 1].mean())
         line = {
             "mode": "accuracy", "workload": w["name"], "precision": name, "time_steps": w["steps"],
-            "reference": "FP64 GPU path (oracle parity 1e-12)",
+            "reference": "FP64 GPU path over the same run",
             "err_n_rel_max": float(np.abs(mr[:, 0] - m64[:, 0]).max() / np.abs(m64[:, 0]).max()),
             "err_u_over_lid_speed_max": float(np.abs(mr[:, 1:3] - m64[:, 1:3]).max() / uw),
             "err_theta_rel_max": float(np.abs(mr[:, 3] - m64[:, 3]).max() / np.abs(m64[:, 3]).max()),
@@ -507,9 +676,12 @@ def batch_arm(args, world, rank, local, pg):
     """The batched workload: 64 uneven cavities and 16 shocks, FP32 state
     in one bgk_batch, tiles chosen by the autotuner; a benchmark step is
     --time-steps (default 20) steps of every instance, continuing the
-    evolution from the initial states set once before the warm-up."""
+    evolution from the initial states set once before the warm-up.  The
+    end-to-end leg sets every instance's state from pinned host memory,
+    steps it and reads its moments back, per benchmark step."""
     import torch
 
+    from paper_0903_4044_gb300 import bgk as B
     from paper_0903_4044_gb300 import build, solver
     from paper_0903_4044_gb300 import workloads as W
 
@@ -524,15 +696,6 @@ def batch_arm(args, world, rank, local, pg):
     nsteps = args.time_steps or 20
     pts = b.points()
 
-    def reinit():
-        for w, s in zip(ws, b.solvers):
-            if w["kind"] == "shock":
-                up, down = solver.B.bgk_rankine_hugoniot(w["mach"], solver.GAMMA)
-                s.init_step(0.0, up, down)
-            else:
-                s.init_uniform((1.0, 0.0, 0.0, 1.0), None, 0.0)
-
-    reinit()
     for _ in range(args.warmup):
         b.step(nsteps)
     torch.cuda.synchronize()
@@ -549,21 +712,62 @@ def batch_arm(args, world, rank, local, pg):
     b.sync()
     elapsed = max_over_ranks(pg, ev0.elapsed_time(ev1) / 1e3)
     value = world * pts * nsteps * args.steps / elapsed
+
+    e2e = None
+    if not args.no_e2e:
+        # one pinned host buffer holding every instance's state (ABI layout,
+        # FP64) and one for every instance's moments
+        offs, moffs, o, mo = [], [], 0, 0
+        for s_ in b.solvers:
+            offs.append(o)
+            moffs.append(mo)
+            o += s_.ncell * s_.nv * 2
+            mo += s_.ncell * 4
+        host = torch.empty(o, dtype=torch.float64, pin_memory=True)
+        mom = torch.empty(mo, dtype=torch.float64, pin_memory=True)
+        hv, mv = host.numpy(), mom.numpy()
+        for s_, off in zip(b.solvers, offs):
+            B.bgk_get_state(s_.h, hv[off:off + s_.ncell * s_.nv * 2])
+
+        def e2e_step():
+            for s_, off in zip(b.solvers, offs):
+                B.bgk_set_state(s_.h, hv[off:off + s_.ncell * s_.nv * 2])   # H2D
+            b.step(nsteps)
+            for s_, mo_ in zip(b.solvers, moffs):
+                B.bgk_moments(s_.h, mv[mo_:mo_ + s_.ncell * 4], 0)          # D2H
+        e2e_step()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+        e2e = {"value": world * pts * nsteps * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(o * 8), "d2h_bytes_per_step": int(mo * 8)}
+        del host, mom
+
+    peaks = load_peaks()
+    hbm = BYTES_PER_UPDATE["f32"] * pts * nsteps * args.steps / elapsed / 1e9
+    roof = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": hbm / peaks["hbm_gbs"], "peak_source": peaks["source"], "traffic": None,
+            "kernel": ("bgk::batch_persistent_kernel" if args.persistent else
+                       "all step kernels of the batch (bgk::step_mixed_kernel, step_mixed_pipe_kernel, "
+                       "step_mixed1d_kernel)"),
+            "bytes_per_update": BYTES_PER_UPDATE["f32"],
+            "note": "algorithmic bytes of every instance (16 B per point and time step) over the whole batch step"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        label, updates, run, _ = reference_sampler("batch", None)
+        dt, threads = run()
+        cpu = {"value": updates / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{label} ({dt:.1f} s; FP64 oracle)", "cpu_model": cpu_model()}
     if rank == 0:
-        tiles = sorted({int(s.info.tile_cells) for s in b.solvers})
+        tiles = sorted({int(s_.info.tile_cells) for s_ in b.solvers})
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch_64_cavities_16_shocks_seed0", "instances": len(ws), "points": pts,
-                       "launch": "one persistent cooperative kernel per benchmark step (grid barrier between "
-                                 "time steps), captured in a CUDA graph" if args.persistent else
-                                 "one CUDA graph per benchmark step, one branch of step kernels per instance",
-                       "time_steps": nsteps, "tiles_chosen": tiles,
-                       "note": "FP32 state in every instance; "
-                               "inputs larger than L2 (9.4 GB of state)"},
-            "roofline": {"bound": "hbm", "note": "mixed workload; see per-kernel lines"},
-            "cpu_baseline": None, "e2e": None, "clocks": clk.summary(),
+            "config": config_for(args, None, world), "tiles_chosen": tiles,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": args.steps if args.persistent else len(ws) * nsteps * args.steps,
         }), flush=True)
     b.close()
@@ -578,7 +782,7 @@ ADJ_BYTES_PER_UPDATE = {"forward": 32.0, "recompute": 32.0, "adj_step": 48.0}
 ADJ_FLOPS_PER_UPDATE = {"forward": 24.0, "recompute": 24.0, "adj_step": 37.0}
 
 
-def adjoint_arm(args, world, rank, local, pg):
+def adjoint_arm(args, w, world, rank, local, pg):
     """Gradient of the lid-integrated shear (128^2 cells, 32^2 velocities,
     Kn 0.1, lid Mach 0.1, 2000 FP64 steps, a checkpoint every 100 steps) with
     respect to Kn, the lid speed and every entry of f0.  A benchmark step is
@@ -593,9 +797,6 @@ def adjoint_arm(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     build.build()
     stream = torch.cuda.current_stream()
-    w = W.CAVITY_128
-    if args.time_steps is not None:
-        w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
     ncell, nv, _ = sizes(w)
     nsteps, K = w["steps"], args.checkpoint_every
     xi = W.perturbation(w.get("seed", 0), ncell, nv)
@@ -667,12 +868,8 @@ def adjoint_arm(args, world, rank, local, pg):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"adjoint_{w['name']}", "cells": ncell, "velocities": nv, "time_steps": nsteps,
-                       "checkpoint_every": K, "objective": "lid-integrated shear",
-                       "gradients": "Kn, lid speed, every entry of f0",
-                       "update": "one (cell, velocity) point of one differentiated time step",
-                       "J": out[0], "dJ_dlnL": out[1], "dJ_dUW": out[2],
-                       "l2": "inputs larger than L2 (268 MB state, 27 GB of segment states)"},
+            "config": config_for(args, w, world),
+            "result": {"J": out[0], "dJ_dlnL": out[1], "dJ_dUW": out[2]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             # forward, recomputation, one reverse kernel per step plus the
             # final streaming adjoint, lid table and seed
@@ -773,9 +970,7 @@ def shock3v_arm(args, w, world, rank, local, pg):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "cells": ncell, "velocities": nv, "time_steps": nsteps,
-                       "max_courant": s.info.max_courant, "parallelism": f"replica x{world}",
-                       "l2": "flushed (256 MB write) between timed steps; state larger than L2"},
+            "config": config_for(args, w, world), "max_courant": s.info.max_courant,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": args.steps * nsteps,
         }), flush=True)
@@ -787,7 +982,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="cavity64")
+    ap.add_argument("--workload", default="cavity256")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="cavity256: skip the FP32 and BF16-deviation forms and their oracle errors")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
@@ -805,36 +1002,39 @@ def main():
                     help="batch workload: one persistent cooperative launch per benchmark step")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
-    w = workload(args.workload) if args.workload not in ("batch", "adjoint", "shock3v", "shock3v_m15") else None
-    if args.time_steps is not None and w is not None and args.time_steps != w["steps"]:
-        w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
+    w = resolve_workload(args)
     if args.impl == "reference":
         reference_arm(args, w, rank, pg)
-        if pg is not None:
-            pg.destroy_process_group()
-        return
-    if args.workload in ("shock3v", "shock3v_m15"):
-        from paper_0903_4044_gb300 import workloads as W
-
-        w3 = W.SHOCK3V_M3 if args.workload == "shock3v" else W.SHOCK3V_M15
-        if args.time_steps is not None:
-            w3 = dict(w3, steps=args.time_steps, name=f"{w3['name']}_{args.time_steps}steps")
-        shock3v_arm(args, w3, world, rank, local, pg)
-        if pg is not None:
-            pg.destroy_process_group()
-        return
-    if args.workload in ("batch", "adjoint"):
-        (batch_arm if args.workload == "batch" else adjoint_arm)(args, world, rank, local, pg)
-        if pg is not None:
-            pg.destroy_process_group()
-        return
-    if args.accuracy:
+    elif args.workload in ("shock3v", "shock3v_m15"):
+        shock3v_arm(args, w, world, rank, local, pg)
+    elif args.workload == "batch":
+        batch_arm(args, world, rank, local, pg)
+    elif args.workload == "adjoint":
+        adjoint_arm(args, w, world, rank, local, pg)
+    elif args.accuracy:
         if rank == 0:
             accuracy_arm(args, w)
     else:
         ours_arm(args, w, world, rank, local, pg)
     if pg is not None:
         pg.destroy_process_group()
+
+
+def resolve_workload(args):
+    """Raw parameters of --workload with --time-steps applied (None for the batch)."""
+    from paper_0903_4044_gb300 import workloads as W
+
+    if args.workload == "batch":
+        return None
+    if args.workload == "adjoint":
+        w = W.CAVITY_128
+    elif args.workload in ("shock3v", "shock3v_m15"):
+        w = W.SHOCK3V_M3 if args.workload == "shock3v" else W.SHOCK3V_M15
+    else:
+        w = workload(args.workload)
+    if args.time_steps is not None and args.time_steps != w["steps"]:
+        w = dict(w, steps=args.time_steps, name=f"{w['name']}_{args.time_steps}steps")
+    return w
 
 
 if __name__ == "__main__":

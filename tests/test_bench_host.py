@@ -41,3 +41,34 @@ def test_traffic_keys_are_benchmark_workload_names():
 def test_cpu_model_names_the_architecture():
     m = bench.cpu_model()
     assert isinstance(m, str) and m.endswith(f"({platform.machine()})")
+
+
+def _args(**kw):
+    import argparse
+
+    d = dict(workload="cavity256", precision="f64", time_steps=None, checkpoint_every=100, persistent=False,
+             gpus=1)
+    d.update(kw)
+    return argparse.Namespace(**d)
+
+
+def test_both_arms_print_the_same_config():
+    # the reference arm and the GPU arm build `config` from the same function
+    # and the same resolved workload, so the driver can pair their lines
+    for wl in ("cavity256", "cavity64", "shock", "adjoint", "shock3v", "batch"):
+        a = _args(workload=wl)
+        w = bench.resolve_workload(a)
+        c = bench.config_for(a, w, 1)
+        assert c == bench.config_for(_args(workload=wl), bench.resolve_workload(_args(workload=wl)), 1)
+        assert "workload" in c and "l2" in c and "precision" in c
+    d = bench.config_for(_args(), bench.resolve_workload(_args()), 1)
+    assert d["workload"] == bench.CAVITY256_200
+    assert d["cells"] == 256 * 256 and d["velocities"] == 48 * 48 and d["time_steps"] == 200
+
+
+def test_default_workload_is_the_256_cavity():
+
+    import inspect
+
+    src = inspect.getsource(bench.main)
+    assert 'default="cavity256"' in src
