@@ -86,6 +86,15 @@ __device__ __forceinline__ void warp_reduce4_ff(float (&h)[4], float (&l)[4], fl
   ff_xor(oh, ol, 1);
 }
 
+// ---- (g, h) pairs on the paired FP32 pipe ------------------------------------
+// FFMA2 / FADD2 / FMUL2 apply one FP32 operation to both members of a pair
+// with the rounding of the scalar operation, so these give the results of
+// the scalar code at half the instructions.
+__device__ __forceinline__ float2 splat(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
 // ---- storage --------------------------------------------------------------
 template <int PREC>
 struct Store;
@@ -212,10 +221,12 @@ __device__ __forceinline__ void flux_form(const MixedTables& M, int vi, const fl
   const float4 a4 = *reinterpret_cast<const float4*>(M.ax + vi_jx(vi));
   const float ax[4] = {a4.x, a4.y, a4.z, a4.w};
   const float ay = M.ay[vi_jy(vi)];
+  const float2 m1 = splat(-1.f), nay = splat(-ay);
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    ft[p].x = fmaf(-ay, f0[p].x - fy[p].x, fmaf(-ax[p], f0[p].x - fx[p].x, f0[p].x));
-    ft[p].y = fmaf(-ay, f0[p].y - fy[p].y, fmaf(-ax[p], f0[p].y - fx[p].y, f0[p].y));
+    const float2 dx = fma2(fx[p], m1, f0[p]);  // f - f_upx, rounded once
+    const float2 dy = fma2(fy[p], m1, f0[p]);
+    ft[p] = fma2(nay, dy, fma2(splat(-ax[p]), dx, f0[p]));
   }
 }
 
@@ -268,37 +279,35 @@ __device__ __forceinline__ void stream_group(const Params& P, const MixedTables&
   flux_form(M, vi, f0, fx, fy, ft);
 }
 
-// A2 for the 4 velocities j0..j0+3: their contributions to (sum g,
-// sum c_x g, sum c_y g, sum |c|^2 g + h) in the lane's Kahan sums.
-__device__ __forceinline__ void group_sums(const MixedTables& M, int vi, const float2 (&ft)[4], float (&hs)[4],
-                                           float (&cs)[4]) {
+// A2 for the 4 velocities j0..j0+3: their contributions to the lane's FP32
+// partial sums s01 = (sum g, sum c_x g), s23 = (sum c_y g, sum |c|^2 g + h).
+// A lane sums at most 4 MGL velocities of a cell this way; the lanes'
+// partials are then combined in float-float (warp_reduce4_ff and the tree
+// over the cell's warps).
+__device__ __forceinline__ void group_sums(const MixedTables& M, int vi, const float2 (&ft)[4], float2& s01,
+                                           float2& s23) {
   const float4 c4 = *reinterpret_cast<const float4*>(M.cx + vi_jx(vi));
   const float cx[4] = {c4.x, c4.y, c4.z, c4.w};
   const float cy = M.cy[vi_jy(vi)];
-  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+  const float cy2 = cy * cy;
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    const float c2 = fmaf(cx[p], cx[p], cy * cy);
-    p0 += ft[p].x;
-    p1 = fmaf(cx[p], ft[p].x, p1);
-    p2 = fmaf(cy, ft[p].x, p2);
-    p3 = fmaf(c2, ft[p].x, p3) + ft[p].y;
+    const float2 gg = splat(ft[p].x);
+    s01 = fma2(make_float2(1.f, cx[p]), gg, s01);
+    s23 = fma2(make_float2(cy, fmaf(cx[p], cx[p], cy2)), gg, s23);
+    s23.y += ft[p].y;
   }
-  kahan(hs[0], cs[0], p0);
-  kahan(hs[1], cs[1], p1);
-  kahan(hs[2], cs[2], p2);
-  kahan(hs[3], cs[3], p3);
 }
 
 // A1 + A2 for the 4 velocities j0..j0+3: f~ into ft, their contributions
 // to the lane's Kahan sums.
 template <int PREC>
 __device__ __forceinline__ void stream_sum_group(const Params& P, const MixedTables& M, const void* fin,
-                                                 const CellCtx& C, int j0, float2 (&ft)[4], float (&hs)[4],
-                                                 float (&cs)[4]) {
+                                                 const CellCtx& C, int j0, float2 (&ft)[4], float2& s01,
+                                                 float2& s23) {
   const int vi = M.vinfo[j0];
   stream_group<PREC>(P, M, fin, C, j0, vi, ft);
-  group_sums(M, vi, ft, hs, cs);
+  group_sums(M, vi, ft, s01, s23);
 }
 
 // A4 for the 4 velocities j0..j0+3: r holds f~ (stored representation) and
@@ -309,22 +318,19 @@ __device__ __forceinline__ void relax_group(const MixedTables& M, const float* p
                                             float a, float kappa, float2 (&r)[4]) {
   const int vi = M.vinfo[j0];
   const float4 xv = *reinterpret_cast<const float4*>(px + vi_jx(vi));
-  const float yv = py[vi_jy(vi)];
-  const float ph[4] = {xv.x * yv, xv.y * yv, xv.z * yv, xv.w * yv};
+  const float2 yv = splat(py[vi_jy(vi)]);
+  const float2 ph01 = mul2(make_float2(xv.x, xv.y), yv), ph23 = mul2(make_float2(xv.z, xv.w), yv);
+  const float ph[4] = {ph01.x, ph01.y, ph23.x, ph23.y};
   float2 mb[4];
   if (Store<PREC>::delta) {
     const float4* m4 = reinterpret_cast<const float4*>(M.mabs + j0);
     unpack_f32(m4[0], m4[1], mb);
   }
+  const float2 na = splat(-a), k1 = make_float2(1.f, kappa);
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    float fg = r[p].x, fh = r[p].y;  // full f~ for the a f~ term
-    if (Store<PREC>::delta) {
-      fg += mb[p].x;
-      fh += mb[p].y;
-    }
-    r[p].x += fmaf(-a, fg, ph[p]);
-    r[p].y += fmaf(-a, fh, kappa * ph[p]);
+    const float2 f = Store<PREC>::delta ? add2(r[p], mb[p]) : r[p];  // full f~ for the a f~ term
+    r[p] = add2(r[p], fma2(na, f, mul2(k1, splat(ph[p]))));     // + (a Phi - a f~), Phi_h = kappa Phi_g
   }
 }
 
@@ -332,11 +338,11 @@ __device__ __forceinline__ void relax_group(const MixedTables& M, const float* p
 // sum |c_n| g over c_n < 0 of the cell's own (full) state (every warp of the
 // cell computes it for itself).
 template <int PREC>
-__device__ __forceinline__ CellCtx cell_ctx(const Params& P, const MixedTables& M, const void* fin, int cell) {
+__device__ __forceinline__ CellCtx cell_ctx(const Params& P, const MixedTables& M, const void* fin, int cell,
+                                            int ix, int iy) {
   using S = Store<PREC>;
   const int lane = threadIdx.x & 31;
   const int nv = P.nv, nx = P.nx;
-  const int ix = cell % nx, iy = cell / nx;
   CellCtx C;
   C.c0 = (size_t)cell * nv;
   C.row = (size_t)nx * nv;
@@ -553,19 +559,23 @@ __device__ __forceinline__ void cell_factors(const Params& P, const MixedTables&
   }
 }
 
-// Stochastic rounding of an FP32 value to BF16: add 16 bits of a hash of the
-// value and its position below the kept bits, then truncate.  Unbiased, so
-// per-step updates smaller than half a BF16 ulp of the deviation survive on
-// average instead of being rounded away every step.
-__device__ __forceinline__ unsigned bf16_sr(float x, unsigned salt) {
-  const unsigned u = __float_as_uint(x);
-  unsigned h = u * 0x9E3779B1u ^ salt;
-  h ^= h >> 16;
-  h *= 0x85EBCA6Bu;
-  h ^= h >> 13;
-  h *= 0xC2B2AE35u;
-  h ^= h >> 16;
-  return (u + (h & 0xFFFFu)) >> 16;
+// Stochastic rounding of an FP32 pair (g, h) to two BF16 values packed in
+// one word: add 16 bits of dither below the kept bits of each value, then
+// keep the top halves.  Rounding up happens with probability equal to the
+// discarded fraction, so the rounding is unbiased and per-step updates
+// smaller than half a BF16 ulp of the deviation survive on average instead
+// of being rounded away every step.  Both dithers come from one 32-bit hash
+// of the pair's bits and its position (a multiply-xorshift mix in the style
+// of MurmurHash3's finaliser): the low half for g, the high half for h.
+__device__ __forceinline__ unsigned bf16x2_sr(float2 v, unsigned salt) {
+  const unsigned ug = __float_as_uint(v.x), uh = __float_as_uint(v.y);
+  unsigned k = (ug ^ salt) * 0x9E3779B1u + uh;
+  k ^= k >> 15;
+  k *= 0x85EBCA6Bu;
+  k ^= k >> 13;
+  k *= 0xC2B2AE35u;
+  k ^= k >> 16;
+  return __byte_perm(ug + (k & 0xFFFFu), uh + (k >> 16), 0x7632);
 }
 
 template <int PREC>
@@ -574,10 +584,7 @@ __device__ __forceinline__ void store_result(void* fout, size_t c0, int j0, int 
     const size_t idx = c0 + j0;
     unsigned w[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const unsigned salt = (unsigned)(idx + p) * 2u;
-      w[p] = bf16_sr(r[p].x, salt) | (bf16_sr(r[p].y, salt + 1u) << 16);
-    }
+    for (int p = 0; p < 4; ++p) w[p] = bf16x2_sr(r[p], (unsigned)(idx + p));
     *reinterpret_cast<uint4*>(static_cast<unsigned*>(fout) + idx) = make_uint4(w[0], w[1], w[2], w[3]);
   } else {
     Store<PREC>::store4(fout, c0, j0, ng, r);
@@ -617,17 +624,15 @@ __device__ __forceinline__ void mixed2d_block(const Params& P, const MixedTables
   float2 ft[MGL][4];
   CellCtx C;
   if (live) {
-    C = cell_ctx<PREC>(P, M, fin, cell);
+    C = cell_ctx<PREC>(P, M, fin, cell, cell % P.nx, cell / P.nx);
     // A1 + A2: stream this lane's groups, float-float moment sums
-    float hs[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
+    float2 s01 = make_float2(0.f, 0.f), s23 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < MGL; ++k) {
       const int g = lic + k * 32 * WPC;
-      if (g < ngroups) stream_sum_group<PREC>(P, M, fin, C, 4 * g, ft[k], hs, cs);
+      if (g < ngroups) stream_sum_group<PREC>(P, M, fin, C, 4 * g, ft[k], s01, s23);
     }
-    float ls[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) ls[k] = -cs[k];
+    float hs[4] = {s01.x, s01.y, s23.x, s23.y}, ls[4] = {0.f, 0.f, 0.f, 0.f};
     float oh, ol;
     warp_reduce4_ff(hs, ls, oh, ol);
     if ((lane & 7) == 0) s_part[c][wc][lane >> 3] = make_float2(oh, ol);
@@ -719,25 +724,26 @@ __global__ void __launch_bounds__(256, (PREC == PREC_F32 && MGL >= 6) ? 2 : 3)
 // map, same summation order), so the two give identical states; the
 // persistent batch kernel runs the block.
 constexpr int kPipeMath = 2;
-constexpr int kPipeThreads = 32 * (8 + kPipeMath);
-constexpr int kPipeBar = 32 * 9;  // threads at each named barrier: 8 streaming warps + one parameter warp
-constexpr size_t kPipeMaxSmem = 72 * 1024;  // dynamic shared memory of one pipelined CTA at most (3 per SM)
+constexpr size_t kPipeMaxSmem = 72 * 1024;  // dynamic shared memory of one pipelined CTA at most
 
-// Barrier ids as immediates (a register id would reserve all 16).
+// Barrier ids and thread counts as immediates (a register id would reserve
+// all 16); NT threads take part: the streaming warps and one parameter warp.
+template <int NT>
 __device__ __forceinline__ void bar_sync_id(int id) {
   switch (id) {
-    case 1: asm volatile("bar.sync 1, %0;" ::"n"(kPipeBar) : "memory"); break;
-    case 2: asm volatile("bar.sync 2, %0;" ::"n"(kPipeBar) : "memory"); break;
-    case 3: asm volatile("bar.sync 3, %0;" ::"n"(kPipeBar) : "memory"); break;
-    default: asm volatile("bar.sync 4, %0;" ::"n"(kPipeBar) : "memory"); break;
+    case 1: asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); break;
+    case 2: asm volatile("bar.sync 2, %0;" ::"n"(NT) : "memory"); break;
+    case 3: asm volatile("bar.sync 3, %0;" ::"n"(NT) : "memory"); break;
+    default: asm volatile("bar.sync 4, %0;" ::"n"(NT) : "memory"); break;
   }
 }
+template <int NT>
 __device__ __forceinline__ void bar_arrive_id(int id) {
   switch (id) {
-    case 1: asm volatile("bar.arrive 1, %0;" ::"n"(kPipeBar) : "memory"); break;
-    case 2: asm volatile("bar.arrive 2, %0;" ::"n"(kPipeBar) : "memory"); break;
-    case 3: asm volatile("bar.arrive 3, %0;" ::"n"(kPipeBar) : "memory"); break;
-    default: asm volatile("bar.arrive 4, %0;" ::"n"(kPipeBar) : "memory"); break;
+    case 1: asm volatile("bar.arrive 1, %0;" ::"n"(NT) : "memory"); break;
+    case 2: asm volatile("bar.arrive 2, %0;" ::"n"(NT) : "memory"); break;
+    case 3: asm volatile("bar.arrive 3, %0;" ::"n"(NT) : "memory"); break;
+    default: asm volatile("bar.arrive 4, %0;" ::"n"(NT) : "memory"); break;
   }
 }
 
@@ -748,12 +754,19 @@ __host__ __device__ __forceinline__ size_t pipe_smem_bytes(const Params& P) {
   return sizeof(float4) * 4 * (size_t)(P.nv / 4) + ((sizeof(float) * 2 * (size_t)(P.nvx + P.nvy) + 15) & ~(size_t)15);
 }
 
-template <int PREC, int MGL>
-__global__ void __launch_bounds__(kPipeThreads, 3)
+template <int NSW>
+constexpr int pipe_threads() { return 32 * (NSW + kPipeMath); }
+
+// NSW streaming warps (group g of a cell goes to thread g mod 32 NSW, as in
+// the block of 8 / NSW cells per CTA) and two parameter warps.
+template <int PREC, int MGL, int NSW>
+__global__ void __launch_bounds__(pipe_threads<NSW>(), NSW == 8 ? 3 : 4)
     step_mixed_pipe_kernel(const void* __restrict__ fin, void* __restrict__ fout, float2* __restrict__ msum,
                            const Params P, const MixedTables M, int* __restrict__ err) {
+  constexpr int NT = 32 * (NSW + 1);
+  constexpr int NST = 32 * NSW;
   extern __shared__ float4 smemf4[];
-  __shared__ float2 s_part[2][8][4];
+  __shared__ float2 s_part[2][NSW][4];
   __shared__ CellPar s_cp[2];
   const int ngroups = P.nv >> 2;
   const int nf = P.nvx + P.nvy;
@@ -761,20 +774,20 @@ __global__ void __launch_bounds__(kPipeThreads, 3)
   float* fac = reinterpret_cast<float*>(smemf4 + 4 * ngroups);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  if (warp >= 8) {  // phase 2 of every second cell, buffer m
-    const int m = warp - 8;
+  if (warp >= NSW) {  // phase 2 of every second cell, buffer m
+    const int m = warp - NSW;
     float* px = fac + m * nf;
     float* py = px + P.nvx;
     for (int cell = blockIdx.x + m * gridDim.x; cell < ncell; cell += kPipeMath * gridDim.x) {
-      bar_sync_id(1 + m);
+      bar_sync_id<NT>(1 + m);
       CellPar cp;
-      cell_moments<PREC, 8>(P, M, cell, 0, s_part[m], cp, msum);
-      // the Gaussians in chunks of 32 as the block's 8 warps take them,
+      cell_moments<PREC, NSW>(P, M, cell, 0, s_part[m], cp, msum);
+      // the Gaussians in chunks of 32 as the block's NSW warps take them,
       // each chunk's central sums totalled over the warp, chunks in order
       float Mx[5], My[5];
-      for (int w = 0; w < 8 && 32 * w < nf; ++w) {
+      for (int w = 0; w < NSW && 32 * w < nf; ++w) {
         float ax[5], ay[5];
-        cell_gauss<8>(P, M, w, cp, px, py, ax, ay);
+        cell_gauss<NSW>(P, M, w, cp, px, py, ax, ay);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
           ax[k] = warp_sum_f(ax[k]);
@@ -790,7 +803,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3)
         if (!cp.ok) atomicOr(err, ERR_MOMENT);
       }
       __syncwarp();
-      bar_arrive_id(3 + m);
+      bar_arrive_id<NT>(3 + m);
     }
     return;
   }
@@ -799,34 +812,35 @@ __global__ void __launch_bounds__(kPipeThreads, 3)
   int b = 0;
   size_t prev_c0 = 0;
   bool have_prev = false;
+  // coordinates of the cell, advanced by gridDim.x cells per iteration
+  const int dix = gridDim.x % P.nx, diy = gridDim.x / P.nx;
+  int ix = blockIdx.x % P.nx, iy = blockIdx.x / P.nx;
   for (int cell = blockIdx.x;; cell += gridDim.x) {
     const bool live = cell < ncell;
     if (live) {  // A1 + A2 of this cell into buffer b
-      const CellCtx C = cell_ctx<PREC>(P, M, fin, cell);
+      const CellCtx C = cell_ctx<PREC>(P, M, fin, cell, ix, iy);
       float4* flo = smemf4 + (size_t)(2 * b) * ngroups;
       float4* fhi = flo + ngroups;
-      float hs[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
+      float2 s01 = make_float2(0.f, 0.f), s23 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < MGL; ++k) {
-        const int g = tid + 256 * k;
+        const int g = tid + NST * k;
         if (g < ngroups) {
           float2 ft[4];
-          stream_sum_group<PREC>(P, M, fin, C, 4 * g, ft, hs, cs);
+          stream_sum_group<PREC>(P, M, fin, C, 4 * g, ft, s01, s23);
           flo[g] = make_float4(ft[0].x, ft[0].y, ft[1].x, ft[1].y);
           fhi[g] = make_float4(ft[2].x, ft[2].y, ft[3].x, ft[3].y);
         }
       }
-      float ls[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) ls[k] = -cs[k];
+      float hs[4] = {s01.x, s01.y, s23.x, s23.y}, ls[4] = {0.f, 0.f, 0.f, 0.f};
       float oh, ol;
       warp_reduce4_ff(hs, ls, oh, ol);
       if ((lane & 7) == 0) s_part[b][warp][lane >> 3] = make_float2(oh, ol);
-      bar_arrive_id(1 + b);
+      bar_arrive_id<NT>(1 + b);
     }
     if (have_prev) {  // A4 of the previous cell from buffer b ^ 1
       const int pb = b ^ 1;
-      bar_sync_id(3 + pb);
+      bar_sync_id<NT>(3 + pb);
       const CellPar cp = s_cp[pb];
       const float* px = fac + pb * nf;
       const float* py = px + P.nvx;
@@ -834,7 +848,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3)
       const float4* fhi = flo + ngroups;
 #pragma unroll
       for (int k = 0; k < MGL; ++k) {
-        const int g = tid + 256 * k;
+        const int g = tid + NST * k;
         if (g < ngroups) {
           float2 r[4];
           unpack_f32(flo[g], fhi[g], r);
@@ -847,6 +861,12 @@ __global__ void __launch_bounds__(kPipeThreads, 3)
     have_prev = true;
     prev_c0 = (size_t)cell * P.nv;
     b ^= 1;
+    ix += dix;
+    iy += diy;
+    if (ix >= P.nx) {
+      ix -= P.nx;
+      ++iy;
+    }
   }
 }
 
@@ -1314,27 +1334,31 @@ cudaError_t dispatch_mgl(const Params& P, const MixedTables& M, const void* fin,
   return cudaErrorInvalidValue;
 }
 
-// Groups of 4 velocities per streaming thread of the pipelined kernel (at
-// most 4: a cell has at most 4096 velocities); 0 if more.
-int pipe_groups(const Params& P) {
-  const int need = (P.nv / 4 + 255) / 256;
+// Groups of 4 velocities per streaming thread of the pipelined kernel with
+// nsw streaming warps (a cell has at most 4096 velocities); 0 if more than 4.
+int pipe_groups(const Params& P, int nsw) {
+  const int need = (P.nv / 4 + 32 * nsw - 1) / (32 * nsw);
   return need <= 4 ? need : 0;
 }
 
-template <int PREC, int MGL>
+template <int PREC, int MGL, int NSW>
 cudaError_t launch_pipe(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
                         int* err, cudaStream_t stream) {
   const size_t smem = pipe_smem_bytes(P);
   int dev = 0, per_sm = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_mixed_pipe_kernel<PREC, MGL>, kPipeThreads, smem);
+    e = cudaFuncSetAttribute(step_mixed_pipe_kernel<PREC, MGL, NSW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPipeMaxSmem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_mixed_pipe_kernel<PREC, MGL, NSW>,
+                                                      pipe_threads<NSW>(), smem);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int ncell = P.nx * P.ny;
   const int grid = per_sm * sms < ncell ? per_sm * sms : ncell;
-  step_mixed_pipe_kernel<PREC, MGL><<<grid, kPipeThreads, smem, stream>>>(fin, fout, msum, P, M, err);
+  step_mixed_pipe_kernel<PREC, MGL, NSW><<<grid, pipe_threads<NSW>(), smem, stream>>>(fin, fout, msum, P, M, err);
   return cudaGetLastError();
 }
 
@@ -1343,11 +1367,11 @@ cudaError_t launch_pipe(const Params& P, const MixedTables& M, const void* fin, 
 template <int PREC>
 cudaError_t dispatch_tile1(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
                            int* err, cudaStream_t stream) {
-  if (pipe_smem_bytes(P) <= kPipeMaxSmem) switch (pipe_groups(P)) {
-      case 1: return launch_pipe<PREC, 1>(P, M, fin, fout, msum, err, stream);
-      case 2: return launch_pipe<PREC, 2>(P, M, fin, fout, msum, err, stream);
-      case 3: return launch_pipe<PREC, 3>(P, M, fin, fout, msum, err, stream);
-      case 4: return launch_pipe<PREC, 4>(P, M, fin, fout, msum, err, stream);
+  if (pipe_smem_bytes(P) <= kPipeMaxSmem) switch (pipe_groups(P, 8)) {
+      case 1: return launch_pipe<PREC, 1, 8>(P, M, fin, fout, msum, err, stream);
+      case 2: return launch_pipe<PREC, 2, 8>(P, M, fin, fout, msum, err, stream);
+      case 3: return launch_pipe<PREC, 3, 8>(P, M, fin, fout, msum, err, stream);
+      case 4: return launch_pipe<PREC, 4, 8>(P, M, fin, fout, msum, err, stream);
     }
   return dispatch_mgl<PREC, 1>(P, M, fin, fout, msum, err, stream);
 }
@@ -1367,7 +1391,7 @@ cudaError_t dispatch_m(const Params& P, const MixedTables& M, const void* fin, v
 }  // namespace
 
 bool mixed_pipe_preferred(const Params& P) {
-  return P.dim == 2 && pipe_smem_bytes(P) <= kPipeMaxSmem && pipe_groups(P) >= 3;
+  return P.dim == 2 && pipe_smem_bytes(P) <= kPipeMaxSmem && pipe_groups(P, 8) >= 3;
 }
 
 size_t step_mixed_smem_bytes(const Params& P, int tile, int prec) { return mixed_smem(P, tile, prec); }
@@ -1383,26 +1407,8 @@ int mixed_groups_per_lane(const Params& P, int tile) {
   return 0;
 }
 
-// The attribute belongs to the kernel: set it once to the pipelined
-// kernel's largest buffers, whatever solver asks first.
-cudaError_t prepare_step_mixed(const Params&, int) {
-  static cudaError_t done = [] {
-    cudaError_t e = cudaSuccess;
-    auto set = [&e](const void* fn) {
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPipeMaxSmem);
-    };
-    set((const void*)step_mixed_pipe_kernel<PREC_F32, 1>);
-    set((const void*)step_mixed_pipe_kernel<PREC_F32, 2>);
-    set((const void*)step_mixed_pipe_kernel<PREC_F32, 3>);
-    set((const void*)step_mixed_pipe_kernel<PREC_F32, 4>);
-    set((const void*)step_mixed_pipe_kernel<PREC_BF16, 1>);
-    set((const void*)step_mixed_pipe_kernel<PREC_BF16, 2>);
-    set((const void*)step_mixed_pipe_kernel<PREC_BF16, 3>);
-    set((const void*)step_mixed_pipe_kernel<PREC_BF16, 4>);
-    return e;
-  }();
-  return done;
-}
+// The pipelined kernels raise their dynamic shared-memory limit at launch.
+cudaError_t prepare_step_mixed(const Params&, int) { return cudaSuccess; }
 
 cudaError_t launch_step_mixed(const Params& P, int prec, const MixedTables& M, const void* fin, void* fout,
                               double4_32a* mom, int* err, cudaStream_t stream) {
