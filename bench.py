@@ -672,6 +672,64 @@ def accuracy_arm(args, w):
         print(json.dumps(line), flush=True)
 
 
+# The paper's table of the drag coefficient D and reduced flow rate G of the
+# main vortex versus the rarefaction parameter delta (Sec. 5, "Results and
+# discussion"): delta -> (D, G) of its parallel code.
+PAPER_DG = {0.1: (0.675, 0.0975), 1.0: (0.624, 0.103), 10.0: (0.393, 0.143)}
+
+
+def dsweep_arm(args):
+    """The cavity of Sec. 5 at delta = 0.1, 1, 10 (side delta mean free
+    paths, 160^2 cells, 20^2 reduced velocities on [-3, 3]^2, lid speed 0.01,
+    FP64) stepped to a steady lid shear, with D and G under the reading stated
+    in the line (the paper does not give their normalisation) and the
+    normalisation-free ratios to delta = 0.1 beside the paper's."""
+    import torch
+
+    from paper_0903_4044_gb300 import build, solver
+
+    build.build()
+    torch.cuda.set_device(0)
+    uw, n, nv = 0.01, 160, 20
+    out = {}
+    for delta, (d_paper, g_paper) in PAPER_DG.items():
+        w = dict(kind="cavity", kn=1.0 / delta, n=n, nv=nv, vbox=(-3.0, 3.0), omega=0.5, cfl=0.5)
+        s = solver.Solver(solver.cavity_config(**w, lid_speed=uw))
+        s.init_uniform((1.0, 0.0, 0.0, 1.0))
+        t0, steps, J, chunk = time.perf_counter(), 0, None, 2000
+        while steps < 400000:
+            s.step(chunk)
+            steps += chunk
+            Jn = s.lid_shear()
+            done = J is not None and abs(Jn - J) < 1e-7 * abs(Jn)
+            J = Jn
+            if done:
+                break
+        mom = s.moments().reshape(n, n, 4)
+        s.close()
+        # D: mean lid shear over the lid length, in units of P0 U_W / v0
+        # (P0 = n0 m v0^2 / 2, v0 = sqrt(2 R T0)); its free-molecular value
+        # is 1 / sqrt(pi) = 0.564
+        D = 2.0 * (J / delta) / uw
+        # G: integral of u_x / U_W along the vertical centre line from the
+        # vortex centre (where u_x changes sign) to the lid, per unit side
+        ux = 0.5 * (mom[:, n // 2 - 1, 1] + mom[:, n // 2, 1]) / uw
+        k0 = int(np.nonzero(ux <= 0.0)[0].max()) + 1 if np.any(ux <= 0.0) else 0
+        G = float(ux[k0:].sum()) / n
+        out[delta] = dict(D=D, G=G, steps=steps, seconds=time.perf_counter() - t0, D_paper=d_paper, G_paper=g_paper)
+    for delta, r in out.items():
+        r["D_over_paper"] = r["D"] / r["D_paper"]
+        r["G_over_paper"] = r["G"] / r["G_paper"]
+        r["D_over_D01"] = r["D"] / out[0.1]["D"]
+        r["D_over_D01_paper"] = r["D_paper"] / PAPER_DG[0.1][0]
+        r["G_over_G01"] = r["G"] / out[0.1]["G"]
+        r["G_over_G01_paper"] = r["G_paper"] / PAPER_DG[0.1][1]
+        print(json.dumps({"mode": "dsweep", "delta": delta, "unpinned": True,
+                          "reading": "D = 2 <tau_xy>_lid / U_W (units P0 U_W / v0); G = int u_x / U_W dy / L "
+                                     "from the vortex centre to the lid on x = L/2",
+                          **r}), flush=True)
+
+
 def batch_arm(args, world, rank, local, pg):
     """The batched workload: 64 uneven cavities and 16 shocks, FP32 state
     in one bgk_batch, tiles chosen by the autotuner; a benchmark step is
@@ -1011,6 +1069,9 @@ def main():
         batch_arm(args, world, rank, local, pg)
     elif args.workload == "adjoint":
         adjoint_arm(args, w, world, rank, local, pg)
+    elif args.workload == "dsweep":
+        if rank == 0:
+            dsweep_arm(args)
     elif args.accuracy:
         if rank == 0:
             accuracy_arm(args, w)
@@ -1024,7 +1085,7 @@ def resolve_workload(args):
     """Raw parameters of --workload with --time-steps applied (None for the batch)."""
     from paper_0903_4044_gb300 import workloads as W
 
-    if args.workload == "batch":
+    if args.workload in ("batch", "dsweep"):
         return None
     if args.workload == "adjoint":
         w = W.CAVITY_128

@@ -142,7 +142,9 @@ typedef struct {
 
 typedef struct bgk_solver bgk_solver;
 
-/* Validate cfg (all checks happen before any CUDA call), build the grids and
+/* The problem statement of Sec. 2.1 (phase-space grid, time step) with the
+ * boundary conditions of Sec. 4.1 (Eq. bc_shock) or Sec. 5.1 (Eq. bc_cavity).
+ * Validate cfg (all checks happen before any CUDA call), build the grids and
  * boundary tables on the current CUDA device, and allocate two state buffers
  * (ping-pong) plus per-cell moment storage.  The state is zero until an
  * init or set_state call.  *out receives the handle (NULL on failure).
@@ -176,8 +178,11 @@ BGK_API bgk_status bgk_init_uniform(bgk_solver* s, const double state[4], const 
 BGK_API bgk_status bgk_set_state(bgk_solver* s, const double* f, int on_device);
 BGK_API bgk_status bgk_get_state(bgk_solver* s, double* f, int on_device);
 
-/* Enqueue nsteps time steps (stream, moments, Maxwellian, relaxation, each
- * step one fused kernel; batches of steps replay a captured CUDA graph).
+/* Enqueue nsteps time steps of the split scheme of Sec. 2.1: free streaming
+ * by Eq. (upwind) (with the integer shift of Eq. (exact) in 1D), the moments
+ * of Eq. (macroscopic), the Maxwellian of Eq. (Maxw) and the relaxation of
+ * Eq. (relaxation); each step is one fused kernel, and batches of steps
+ * replay a captured CUDA graph.
  * Asynchronous.  nsteps = 0 is a no-op; negative is INVALID_ARG. */
 BGK_API bgk_status bgk_step(bgk_solver* s, int64_t nsteps);
 
@@ -186,7 +191,8 @@ BGK_API bgk_status bgk_step(bgk_solver* s, int64_t nsteps);
  * the last step (the values the relaxation used).  Synchronises. */
 BGK_API bgk_status bgk_moments(bgk_solver* s, int which, double* mom, int on_device);
 
-/* Fluxes through one face for each of its cells (ny cells for x faces, nx
+/* Fluxes through one face for each of its cells (the wall fluxes behind the
+ * drag of Sec. 5.2, "Results and discussion"; ny cells for x faces, nx
  * for y faces; 1 for dim 1), out[k][4] = (mass, shear, normal momentum,
  * energy) = sum over velocities of (c_n, c_t c_n, c_n^2, c_n (|c|^2 g + h))
  * times the crossing value times dv, where c_n is along the inward normal
@@ -195,6 +201,14 @@ BGK_API bgk_status bgk_moments(bgk_solver* s, int which, double* mom, int on_dev
  * c_n < 0 and the boundary value the next step would use for c_n > 0.
  * Synchronises. */
 BGK_API bgk_status bgk_wall_fluxes(bgk_solver* s, int face, double* out, int on_device);
+
+/* Lid-integrated shear of the current state (2D only): *J = dx * sum over
+ * the face cells k of the lid (face YHI) of the shear flux tau_k of
+ * bgk_wall_fluxes, summed in the order k = 0 .. nx-1.  This is the drag of
+ * Sec. 5.2, "Results and discussion", before its normalisation, and the
+ * objective that bgk_adjoint_lid_shear differentiates.  J is a host pointer.
+ * Synchronises.  Errors: INVALID_ARG (null pointer), UNSUPPORTED (dim 1). */
+BGK_API bgk_status bgk_lid_shear(bgk_solver* s, double* J);
 
 /* Wait for the solver's stream; report a kernel-detected numerical failure. */
 BGK_API bgk_status bgk_sync(bgk_solver* s);

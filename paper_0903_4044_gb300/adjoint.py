@@ -49,18 +49,16 @@ def lid_shear_and_gradient(spec: dict, f0: torch.Tensor, kn: float, lid_speed: f
 
 
 def lid_shear(spec: dict, f0: torch.Tensor, kn: float, lid_speed: float) -> float:
-    """J alone: nsteps forward steps, then the lid's wall fluxes."""
+    """J alone: nsteps forward steps, then bgk_lid_shear."""
     stream = torch.cuda.current_stream(f0.device).cuda_stream
     with torch.cuda.device(f0.device):
         s = _solver(spec, kn, lid_speed, stream)
         try:
             s.set_state(f0)
             s.step(spec["nsteps"])
-            fl = s.wall_fluxes(B.BGK_FACE_YHI)
-            dx = s.cfg.lx / s.cfg.nx
+            return s.lid_shear()
         finally:
             s.close()
-    return float(dx * fl[:, 1].sum())
 
 
 class LidShear(torch.autograd.Function):

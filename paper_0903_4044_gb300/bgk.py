@@ -31,6 +31,7 @@ EXPORTS = (
     "bgk_batch_destroy", "bgk_autotune", "bgk_batch_autotune", "bgk_adjoint_lid_shear",
     "bgk3v_create", "bgk3v_destroy", "bgk3v_get_info", "bgk3v_init_step", "bgk3v_set_state",
     "bgk3v_get_state", "bgk3v_step", "bgk3v_moments", "bgk3v_sync", "bgk_batch_set_persistent",
+    "bgk_lid_shear",
 )
 
 
@@ -110,6 +111,7 @@ def lib() -> ctypes.CDLL:
             "bgk_moments": ([_P, ctypes.c_int, _P, ctypes.c_int], ctypes.c_int),
             "bgk_wall_fluxes": ([_P, ctypes.c_int, _P, ctypes.c_int], ctypes.c_int),
             "bgk_sync": ([_P], ctypes.c_int),
+            "bgk_lid_shear": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "bgk_rankine_hugoniot": ([ctypes.c_double, ctypes.c_double, _D4, _D4], ctypes.c_int),
             "bgk_last_error": ([], ctypes.c_char_p),
             "bgk_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -231,6 +233,12 @@ def bgk_moments(h: int, out, which: int = 0) -> None:
 def bgk_wall_fluxes(h: int, face: int, out) -> None:
     addr, dev = _ptr(out)
     _check(lib().bgk_wall_fluxes(h, face, addr, dev), "bgk_wall_fluxes")
+
+
+def bgk_lid_shear(h: int) -> float:
+    J = ctypes.c_double()
+    _check(lib().bgk_lid_shear(h, ctypes.byref(J)), "bgk_lid_shear")
+    return J.value
 
 
 def bgk_sync(h: int) -> None:

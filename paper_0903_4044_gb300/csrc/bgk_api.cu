@@ -746,6 +746,28 @@ bgk_status bgk_wall_fluxes(bgk_solver* s, int face, double* out, int on_device) 
   BGK_GUARD_END
 }
 
+bgk_status bgk_lid_shear(bgk_solver* s, double* J) {
+  BGK_GUARD_BEGIN
+  if (!s || !J) return fail(BGK_ERR_INVALID_ARG, "null argument");
+  if (s->P.dim != 2) return fail(BGK_ERR_UNSUPPORTED, "the lid shear needs a 2D solver");
+  bgk_status st = select_device(s);
+  if (st != BGK_OK) return st;
+  std::vector<double4_32a> fl((size_t)s->P.nx);
+  const double2* view = nullptr;
+  cudaError_t e = s->f64_view(&view);
+  if (e == cudaSuccess) e = bgk::launch_wall_fluxes(s->P, s->tables(), view, bgk::YHI, s->flux_tmp, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(fl.data(), s->flux_tmp, sizeof(double4_32a) * fl.size(), cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lid shear");
+  st = check_flag(s);  // synchronises the stream
+  if (st != BGK_OK) return st;
+  double sum = 0.0;
+  for (const double4_32a& f : fl) sum += s->P.dx * f.y;
+  *J = sum;
+  return BGK_OK;
+  BGK_GUARD_END
+}
+
 bgk_status bgk_sync(bgk_solver* s) {
   BGK_GUARD_BEGIN
   if (!s) return fail(BGK_ERR_INVALID_ARG, "null solver");

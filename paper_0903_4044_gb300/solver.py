@@ -82,6 +82,10 @@ class Solver:
         B.bgk_wall_fluxes(self.h, face, out)
         return out
 
+    def lid_shear(self) -> float:
+        """Lid-integrated shear of the current state (bgk_lid_shear)."""
+        return B.bgk_lid_shear(self.h)
+
     @property
     def dt(self) -> float:
         return self.info.dt

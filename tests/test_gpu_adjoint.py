@@ -205,6 +205,59 @@ def test_finite_differences_full_size():
     _fd_checks(W.CAVITY_128, W.CAVITY_128["steps"], 100, 10000)
 
 
+def test_finite_differences_single_entries_full_size():
+    # 20 individual entries of dJ/df0 at full size (128 x 128 cells, 32 x 32
+    # velocities, 2000 steps, a checkpoint every 100): in ten cells (the lid's
+    # corners and middle, the row below it, the interior, the three other
+    # walls) the entry with the largest |dJ/df0| of the cell and one seeded
+    # entry, g or h.  A central difference with h = 1e-6 carries the rounding
+    # of the two forward runs: J is reproduced to about 1e-15 relative, so
+    # the quotient has an absolute noise of about 1e-15 |J| / (2h); the bound
+    # allows ten times that plus 1e-5 relative.
+    import torch
+
+    w = W.CAVITY_128
+    spec = A.cavity_spec(w, w["steps"], 100)
+    f0 = _f0(w)
+    kn, uw = w["kn"], _lid_speed(w)
+    grad = torch.empty_like(f0)
+    J, _, _ = A.lid_shear_and_gradient(spec, f0, kn, uw, grad)
+    g = grad.cpu().numpy()
+    n, nv = w["n"], f0.shape[1]
+    floor = 10 * 1e-15 * abs(J) / (2 * H)
+    cells = [(64, 127), (0, 127), (127, 127), (64, 126), (30, 110), (64, 64), (10, 0), (127, 40), (0, 90),
+             (90, 20)]
+    u = (W.uniform_pm1(17, 2 * len(cells)) + 1.0) * 0.5
+    checked = 0
+    for i, (ix, iy) in enumerate(cells):
+        c = iy * n + ix
+        vmax, kmax = np.unravel_index(np.abs(g[c]).argmax(), g[c].shape)
+        for v, k in ((int(vmax), int(kmax)), (int(u[2 * i] * nv), int(u[2 * i + 1] * 2))):
+            e = torch.zeros_like(f0)
+            e[c, v, k] = H
+            fd = (A.lid_shear(spec, f0 + e, kn, uw) - A.lid_shear(spec, f0 - e, kn, uw)) / (2 * H)
+            ad = g[c, v, k]
+            assert abs(ad - fd) <= TOL_FD * abs(ad) + floor, ((ix, iy), v, k, ad, fd)
+            checked += 1
+    assert checked == 20
+
+
+def test_lid_shear_matches_wall_fluxes():
+    # bgk_lid_shear is dx times the sum of the lid's shear fluxes
+    w = W.scaled(W.CAVITY_64, n=20, nv=24)
+    s = solver.make_cavity(w, xi=W.perturbation(0, 400, 576))
+    s.step(7)
+    fl = s.wall_fluxes(B.BGK_FACE_YHI)
+    dx = s.cfg.lx / s.cfg.nx
+    assert s.lid_shear() == pytest.approx(dx * fl[:, 1].sum(), rel=1e-14)
+    s.close()
+    s = solver.make_shock(W.scaled(W.SHOCK_M2, nx=20))
+    with pytest.raises(B.BgkError) as e:
+        s.lid_shear()
+    assert e.value.status == B.BGK_ERR_UNSUPPORTED
+    s.close()
+
+
 # ---------------------------------------------------------------------------
 # torch.autograd.Function
 # ---------------------------------------------------------------------------
