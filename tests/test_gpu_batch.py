@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import oracle
+import precision_bounds as PB
 from paper_0903_4044_gb300 import bgk as B
 from paper_0903_4044_gb300 import build, solver
 from paper_0903_4044_gb300 import workloads as W
@@ -148,6 +149,38 @@ def test_pipelined_tile1_equals_block():
         assert np.array_equal(sb.get_state(), s.get_state()), w["name"]
         assert np.array_equal(sb.moments(which=1), s.moments(which=1)), w["name"]
         s.close()
+    b.close()
+
+
+def test_persistent_against_oracle():
+    # one FP32 cavity and one FP32 shock stepped 20 times inside a persistent
+    # batch, against the FP64 oracle, within the FP32 bounds of
+    # tests/precision_bounds.py: eps = (6 N + 1) 2^-24 of a moment's sum of
+    # absolute terms, so n within eps, theta within 2 eps, U within eps times
+    # the mean particle speed, at most <|c - U|> + |U| (<|c - U|> <= 2 at the
+    # temperatures of these problems)
+    nsteps = 20
+    eps = PB.f32(nsteps)["n"]
+    ws = [W.scaled(W.CAVITY_64, name="o0", n=16, nv=24, precision="f32", seed=9),
+          W.scaled(W.SHOCK_M2, name="o1", nx=60, precision="f32")]
+    b = solver.Batch(ws)
+    b.set_persistent(True)
+    b.step(nsteps)
+    b.sync()
+    for w, sb in zip(ws, b.solvers):
+        if w["kind"] == "cavity":
+            prob0, _, _ = oracle.cavity_problem(**w)
+            xi = W.perturbation(w["seed"], prob0.ncell, prob0.nv)
+            prob, g, h = oracle.cavity_problem(**w, xi=xi)
+        else:
+            prob, g, h = oracle.shock_problem(**w)
+        g1, h1, _ = oracle.step(prob, g, h, nsteps)
+        want = oracle.state_moments(prob, g1, h1)
+        got = sb.moments()
+        assert np.abs(got[:, 0] - want[:, 0]).max() / np.abs(want[:, 0]).max() <= eps, w["name"]
+        assert np.abs(got[:, 3] - want[:, 3]).max() / np.abs(want[:, 3]).max() <= 2 * eps, w["name"]
+        speed = 2.0 + np.abs(want[:, 1:3]).max()
+        assert np.abs(got[:, 1:3] - want[:, 1:3]).max() <= eps * speed, w["name"]
     b.close()
 
 

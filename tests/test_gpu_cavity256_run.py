@@ -9,39 +9,26 @@ FP64: the per-step rounding of the two paths differs at about 1e-16 and the
 scheme does not amplify it, so every field agrees to 1e-12 (velocities
 relative to the lid speed U_W, the rest relative to the field's scale).
 
-Reduced precisions: bounds from the storage precision, stated before the
-run (N = 2000 steps, nv = 2304 velocities per cell, dv = (10/48)^2, 65536
-cells of side dx = 20/256, lid speed U_W = 0.0456, lid shear tau >= 0.01):
-  FP32 rounds every stored value to 2^-24 relative each step.  With every
-  rounding of the same sign (no cancellation at all), a moment drifts by at
-  most eps = N 2^-24 = 1.19e-4 of its sum of absolute terms: n and the total
-  mass by eps, U by eps <|c|> / U_W = eps (sqrt(pi)/2) / U_W (2.3e-3 of U_W),
-  theta = (2/3)(E/n - U^2) by 2 eps, the lid shear by eps sum |c_x c_y| F /
-  tau <= eps (1/pi) / 0.01 (3.8e-3).
-  BF16 stores d = f - M_abs with stochastic rounding: a store errs by at most
-  one ulp, 2^-7 |d|, with zero mean and standard deviation at most half an
-  ulp, independently across velocities.  The lid drives deviations
-  2 |c| U_W M(c) <= 0.0125 (and 2 c^2 U_W M <= 0.0107 in c d), the seeded
-  perturbation 3.2e-4, density and temperature changes of order Mach^2 less
-  than 8e-4: max|d| <= 0.015, max|c d| <= 0.0123.  One step thus adds to a
-  cell's n an error of standard deviation s_n = sqrt(nv) 2^-8 max|d| dv
-  (1.2e-4), to its n U one of s_u = sqrt(nv) 2^-8 max|c d| dv.  Streaming
-  carries each step's errors away at about 0.05 cells per step (the mean
-  speed times dt / dx), so after k steps they are spread over about
-  0.0079 k^2 cells; summing the variances, sum_k 1 / max(1, 0.0079 k^2) =
-  21.9, a cell's accumulated error has a standard deviation at most
-  sqrt(21.9) s = 4.7 s.  The bounds are six of those: n 28 s_n (3.4e-3), U
-  28 s_u / U_W (6.2e-2 of U_W), theta (2/3)(1 + 1.5) x the n bound (5.7e-3),
-  the lid shear per cell 28 sqrt(nv / 2) 2^-8 max|c_x c_y d| dv / tau with
-  max|c_x c_y d| <= 0.0075 (0.12), J (256 lid cells, errors correlated over
-  about 10) that over sqrt(25.6) (2.4e-2), and the total mass, whose errors
-  do not spread out, 6 sqrt(N cells) s_n dx^2 / 400 (1.3e-4).
+Reduced precisions: the bounds of tests/precision_bounds.py (storage
+precision only, stated before the run) for N = 2000 steps, nv = 2304
+velocities per cell, dv = (10/48)^2, 65536 cells of side dx = 20/256, dt =
+0.00399, lid speed U_W = 0.0456 (Mach 0.05), perturbation amplitude 1e-3:
+FP32 n and mass 7.2e-4, theta 1.4e-3, U 1.4e-2 of U_W; BF16 n 3.3e-3, theta
+5.5e-3, U 8.6e-2 of U_W, mass 1.2e-4.  The lid shear (tau >= 0.01 on the
+lid) gets the n bound times sum |c_x c_y| F / tau <= (1/pi) / 0.01 in FP32;
+in BF16 the sum of the stochastic errors of the nv/2 incident velocities,
+6 spread sqrt(nv / 2) 2^-8 max|c_x c_y d| dv / tau with max|c_x c_y d| <=
+2 U_W max(c_x^2 |c_y| e^{-c^2}) / pi + Mach^2 = 7.1e-3 (0.12), and J,
+averaged over 256 lid cells whose errors are correlated over about 10, that
+over sqrt(25.6) (2.4e-2).
 """
+import math
 import os
 
 import numpy as np
 import pytest
 
+import precision_bounds as PB
 from paper_0903_4044_gb300 import bgk as B
 from paper_0903_4044_gb300 import build, solver
 from paper_0903_4044_gb300 import workloads as W
@@ -50,21 +37,19 @@ pytestmark = pytest.mark.gpu
 
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 STEPS = 2000
-N_, NV, DV, DX, CELLS = 2000, 48 * 48, (10.0 / 48) ** 2, 20.0 / 256, 256 * 256
-EPS32 = N_ * 2.0 ** -24
-UW = 0.05 * (5.0 / 6.0) ** 0.5
+NV, DV, DX, DT, CELLS = 48 * 48, (10.0 / 48) ** 2, 20.0 / 256, 0.5 * (20.0 / 256) / (2 * 4.8958333333333333), 65536
+UW, MACH, AMP = 0.05 * (5.0 / 6.0) ** 0.5, 0.05, 1e-3
 TAU_MIN = 0.01
-S_N = NV ** 0.5 * 2.0 ** -8 * 0.015 * DV
-S_U = NV ** 0.5 * 2.0 ** -8 * 0.0123 * DV
-S_TAU = (NV / 2) ** 0.5 * 2.0 ** -8 * 0.0075 * DV
-SPREAD = sum(1.0 / max(1.0, 0.0079 * k * k) for k in range(1, N_ + 1)) ** 0.5   # 4.7
+_F = PB.f32(STEPS)
+_B = PB.bf16(STEPS, NV, DV, CELLS, DX, DT, UW, MACH, AMP)
+_K = 6 * PB.spread(STEPS, PB.MEAN_SPEED_2D * DT / DX)
+_TAU16 = _K * (NV / 2) ** 0.5 * 2.0 ** -8 * (2 * UW * 0.1578 / math.pi + MACH ** 2) * DV / TAU_MIN
 BOUNDS = {
     "f64": dict(n=1e-12, u=1e-12, theta=1e-12, shear=1e-12, J=1e-12, mass=1e-13),
-    "f32": dict(n=EPS32, u=EPS32 * np.sqrt(np.pi) / 2 / UW, theta=2 * EPS32, shear=EPS32 / np.pi / TAU_MIN,
-                J=EPS32 / np.pi / TAU_MIN, mass=EPS32),
-    "bf16": dict(n=6 * SPREAD * S_N, u=6 * SPREAD * S_U / UW, theta=(2 / 3) * 2.5 * 6 * SPREAD * S_N,
-                 shear=6 * SPREAD * S_TAU / TAU_MIN, J=6 * SPREAD * S_TAU / TAU_MIN / 25.6 ** 0.5,
-                 mass=6 * (N_ * CELLS) ** 0.5 * S_N * DX * DX / 400.0),
+    "f32": dict(n=_F["n"], u=_F["u"] / UW, theta=_F["theta"], shear=_F["n"] / math.pi / TAU_MIN,
+                J=_F["n"] / math.pi / TAU_MIN, mass=_F["mass"]),
+    "bf16": dict(n=_B["n"], u=_B["u"] / UW, theta=_B["theta"], shear=_TAU16, J=_TAU16 / 25.6 ** 0.5,
+                 mass=_B["mass"]),
 }
 
 
@@ -91,15 +76,12 @@ def _lib():
 
 
 def test_bounds_are_the_stated_numbers():
-    # the docstring's figures, recomputed from the formulas above
-    assert EPS32 == pytest.approx(1.19e-4, rel=1e-2)
-    assert BOUNDS["f32"]["u"] == pytest.approx(2.3e-3, rel=2e-2)
-    assert SPREAD == pytest.approx(4.7, rel=1e-2)
-    assert BOUNDS["bf16"]["n"] == pytest.approx(3.4e-3, rel=2e-2)
-    assert BOUNDS["bf16"]["u"] == pytest.approx(6.2e-2, rel=2e-2)
-    assert BOUNDS["bf16"]["theta"] == pytest.approx(5.7e-3, rel=2e-2)
-    assert BOUNDS["bf16"]["J"] == pytest.approx(2.4e-2, rel=2e-2)
-    assert BOUNDS["bf16"]["mass"] == pytest.approx(1.3e-4, rel=2e-2)
+    # the docstring's figures, recomputed from the formulas
+    f, b = BOUNDS["f32"], BOUNDS["bf16"]
+    assert f["n"] == pytest.approx(7.2e-4, rel=2e-2) and f["u"] == pytest.approx(1.4e-2, rel=2e-2)
+    assert b["n"] == pytest.approx(3.3e-3, rel=3e-2) and b["theta"] == pytest.approx(5.5e-3, rel=3e-2)
+    assert b["u"] == pytest.approx(8.6e-2, rel=3e-2) and b["mass"] == pytest.approx(1.2e-4, rel=5e-2)
+    assert b["shear"] == pytest.approx(0.12, rel=5e-2) and b["J"] == pytest.approx(2.4e-2, rel=5e-2)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
