@@ -47,6 +47,8 @@ DETAIL = {"f64": "FP64 state and arithmetic",
                    "normalisation in float-float rounded to FP32")}
 
 
+CAVITY256_200 = "cavity_kn0.05_ma0.05_256x256_v48x48_200steps"
+
 # DRAM bytes per launch of the step kernel from an ncu capture (dram__bytes_
 # read.sum + write.sum), valid only for the kernel sources that were
 # captured and for the kernel that is launched: the SHA-1 of those files
@@ -54,11 +56,21 @@ DETAIL = {"f64": "FP64 state and arithmetic",
 # capture commands sit with the ncu summaries under profiles/.
 MEASURED_TRAFFIC = {
     ("cavity_kn0.1_ma0.1_64x64_v32x32_f64", "f64"): {
-        "bytes": 169.0e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
-        "sha1": "6161cceb9040c0d99beff2594a8ed3676a0d9198", "kernel": "bgk::step_f64_kernel"},
-    ("cavity_kn0.05_ma0.05_256x256_v48x48_200steps", "f32"): {
-        "bytes": 2.53e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
-        "sha1": "4f86d8788e3b61f3090d89fc0957a56b7487dc17", "kernel": "bgk::step_mixed_pipe_kernel"},
+        "bytes": 170.5e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
+        "sha1": "ee36c54afaa1baba33fed398ff86a5920233a0a9", "kernel": "bgk::step_f64_kernel"},
+    # captured on 128^2 x 48^2 (2.4675 GB per launch, 65.4 B per update:
+    # the parked f~ of the resident cells exceeds L2 at 48^2 velocities) and
+    # scaled by the 4x updates of a 256^2 x 48^2 launch
+    (CAVITY256_200, "f64"): {
+        "bytes": 4 * 2.4675e9, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
+        "sha1": "ee36c54afaa1baba33fed398ff86a5920233a0a9", "kernel": "bgk::step_f64_kernel",
+        "note": "captured on 128^2 x 48^2 cells x velocities, scaled by updates"},
+    (CAVITY256_200, "f32"): {
+        "bytes": 2.555e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
+        "sha1": "345749cb3f27dee9b2751393fd8a0b57e95f5693", "kernel": "bgk::step_mixed_pipe_kernel"},
+    (CAVITY256_200, "bf16"): {
+        "bytes": 1.173e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
+        "sha1": "345749cb3f27dee9b2751393fd8a0b57e95f5693", "kernel": "bgk::step_mixed_kernel"},
 }
 
 
@@ -179,9 +191,6 @@ def workload(name: str) -> dict:
     if name == "cavity256_full":
         return W.CAVITY_256
     raise SystemExit(f"unknown workload {name}")
-
-
-CAVITY256_200 = "cavity_kn0.05_ma0.05_256x256_v48x48_200steps"
 
 
 def bench_config(w: dict, precision: str, world: int) -> dict:
@@ -395,6 +404,9 @@ def roofline(w: dict, precision: str, per_launch: float, kname: str, traffic_ove
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peaks["source"]}
     traffic = traffic_override if traffic_override is not None else measured_traffic(w["name"], precision, kname)
+    note = MEASURED_TRAFFIC.get((w["name"], precision), {}).get("note")
+    if traffic is not None and traffic_override is None and note:
+        roof["traffic_note"] = note
     roof.update({"traffic": traffic, "kernel": kname, "launch_ms": per_launch * 1e3,
                  "bytes_per_update": BYTES_PER_UPDATE[precision], "hbm_gbs": hbm_achieved,
                  "hbm_frac": hbm_achieved / peaks["hbm_gbs"]})
