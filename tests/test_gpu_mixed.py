@@ -118,6 +118,56 @@ def test_mixed_conserves_mass(name):
     s.close()
 
 
+def test_bf16_stochastic_rounding_is_unbiased():
+    # A homogeneous bi-Maxwellian (temperatures 1.3, 1.1, 1.2 along x, y, z)
+    # between specular walls: streaming leaves it unchanged and the
+    # relaxation, which conserves n, U and theta, damps the anisotropy
+    # A = sum (c_x^2 - c_y^2) g dv by exactly b = exp(-nu dt) per step (the
+    # discrete Maxwellian of a grid symmetric in c_x and c_y has none).  At
+    # Kn 6 on 16 cells (dt = 1e-3) a step changes a deviation by about 1e-3 of
+    # its distance to the Maxwellian, far below half a BF16 ulp of the
+    # deviation: round-to-nearest storage would leave A where it started,
+    # while unbiased stochastic rounding follows b^N on average.
+    # Bound: each store adds a zero-mean error of standard deviation at most
+    # 2^-8 |d| per value; A's error decays like A, so it settles at a standard
+    # deviation of at most sigma_step / sqrt(2 (1 - b)) per cell,
+    # sigma_step = sqrt(sum (c_x^2 - c_y^2)^2 (2^-8 max|d|)^2) dv, and the mean
+    # over the cells at that over sqrt(cells); the test allows six of those,
+    # plus the initial rounding to nearest, 2^-8 sum |c_x^2 - c_y^2| |d| dv, times b^N.
+    n, nv, box = 16, 32, 5.5
+    side = 1.0 / 6.0
+    cfg = B.make_config(dim=2, nx=n, ny=n, lx=side, ly=side, nvx=nv, nvy=nv, vx=(-box, box), vy=(-box, box),
+                        cfl=0.5, precision=B.BGK_BF16_DEV, bc=[(B.BGK_BC_SPECULAR, 1, 0, 0, 1)] * 4)
+    s = solver.Solver(cfg)
+    c = -box + (np.arange(nv) + 0.5) * (2 * box / nv)
+    cx, cy = np.meshgrid(c, c)          # v = jy * nvx + jx
+    cx, cy = cx.ravel(), cy.ravel()
+    dv = (2 * box / nv) ** 2
+    tx, ty, tz = 1.3, 1.1, 1.2
+    g = np.exp(-cx ** 2 / tx - cy ** 2 / ty) / (np.pi * np.sqrt(tx * ty))
+    f0 = np.stack([g, 0.5 * tz * g], axis=-1)[None].repeat(n * n, axis=0)
+    s.set_state(np.ascontiguousarray(f0))
+    w = cx ** 2 - cy ** 2
+    A0 = float((w * g).sum() * dv)
+    nden = g.sum() * dv
+    theta = (2.0 / 3.0) * (((cx ** 2 + cy ** 2) * g + 0.5 * tz * g).sum() * dv) / nden
+    b = np.exp(-nden * np.sqrt(theta) * s.info.dt)
+    steps = int(round(1.0 / (1.0 - b)))          # nu t = 1
+    s.step(steps)
+    st = s.get_state()
+    s.close()
+    A = float(((st[..., 0] * w[None]).sum(axis=1) * dv).mean())
+    mabs = np.exp(-(cx ** 2 + cy ** 2)) / np.pi
+    geq = nden * np.exp(-(cx ** 2 + cy ** 2) / theta) / (np.pi * theta)
+    dmax = np.maximum(np.abs(g - mabs), np.abs(geq - mabs))
+    sigma = np.sqrt((w ** 2 * (2.0 ** -8 * dmax) ** 2).sum()) * dv / np.sqrt(2 * (1 - b)) / n
+    bound = 6 * sigma + 2.0 ** -8 * (np.abs(w) * np.abs(g - mabs)).sum() * dv * b ** steps
+    want = A0 * b ** steps
+    print(f"A0 {A0:.4f} A {A:.5f} want {want:.5f} bound {bound:.5f}")
+    assert abs(A - want) <= bound, (A, want, bound)
+    assert abs(A0 - want) > 3 * bound          # round-to-nearest (A stuck near A0) would fail
+
+
 @pytest.mark.parametrize("name", ["f32", "bf16"])
 def test_mixed_variants_and_tiles(name):
     # specular walls, Euler relaxation, every tile size, non-square grids
