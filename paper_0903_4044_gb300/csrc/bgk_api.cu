@@ -75,6 +75,7 @@ struct bgk_solver {
   float2* m_ghost = nullptr;
   float2* m_mabs = nullptr;
   double* m_sums = nullptr;  // [12]: mabs sums, emitted, mabs sums as float-float pairs
+  unsigned* m_ctr = nullptr;  // [2] step counter of the BF16 dither (see MixedTables::step_ctr)
   int* err = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int64_t gen = 0;  // bumped whenever captured launches become stale (tile change)
@@ -108,6 +109,7 @@ struct bgk_solver {
     M.emitted = m_sums + 4;
     M.mabs_ff = reinterpret_cast<const float2*>(m_sums + 8);
     M.shift = shift;
+    M.step_ctr = m_ctr;
     return M;
   }
   size_t state_elems() const { return (size_t)P.nx * P.ny * P.nv; }  // (g,h) pairs
@@ -320,7 +322,7 @@ void release(bgk_solver* s) {
     if (g) cudaGraphExecDestroy(g);
   void* bufs[] = {s->f[0], s->f[1], s->stage, s->mom_step, s->mom_tmp, s->flux_tmp, s->cx, s->cy,
                   s->coef, s->shift, s->cxy, s->vinfo, s->ghost, s->emitted, s->m_coef, s->m_cx,
-                  s->m_cy, s->m_ax, s->m_ay, s->m_ghost, s->m_mabs, s->m_sums, s->err};
+                  s->m_cy, s->m_ax, s->m_ay, s->m_ghost, s->m_mabs, s->m_sums, s->m_ctr, s->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -332,7 +334,7 @@ cudaError_t enqueue_step(bgk_solver* s, int from, cudaStream_t st) {
     return bgk::launch_step_f64(s->P, s->tables(), (const double2*)s->f[from], (double2*)s->f[1 - from],
                                 s->mom_step, s->err, st);
   return bgk::launch_step_mixed(s->P, s->prec, s->mtables(), s->f[from], s->f[1 - from], s->mom_step,
-                                s->err, st);
+                                s->err, st, from);
 }
 
 // Write an FP64 state (device pointer, ABI layout) into the current buffer.
@@ -504,6 +506,7 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
     ALLOC(m_ghost, (size_t)bgk::kFaces * P.nv);
     ALLOC(m_mabs, P.nv);
     ALLOC(m_sums, 12);
+    ALLOC(m_ctr, 2);
   }
   ALLOC(mom_step, ncell);
   ALLOC(mom_tmp, ncell);
@@ -523,6 +526,7 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(s->f[1], 0, s->point_bytes() * elems, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->mom_step, 0, sizeof(double4_32a) * ncell, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess && s->m_ctr) e = cudaMemsetAsync(s->m_ctr, 0, 2 * sizeof(unsigned), s->stream);
   if (e == cudaSuccess)
     e = bgk::launch_build_tables(P, s->cx, s->cy, s->coef, s->shift, s->cxy, s->vinfo, s->ghost,
                                  s->emitted, s->stream);

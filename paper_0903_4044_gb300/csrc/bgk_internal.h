@@ -68,6 +68,8 @@ struct MixedTables {
   const float2* mabs_ff;    // [4] the same sums as float-float pairs
   const double* emitted;    // [kFaces] sum_{c_n>0} c_n ghost_g dv of the FP32 ghosts
   const int* shift;         // [nv] 1D integer Courant shift (as Tables::shift)
+  unsigned* step_ctr;       // [2] steps taken: the kernel of buffer parity p reads word p and
+                            //   writes word 1 - p (the BF16 dither varies with it)
 };
 
 // Launchers (bgk_step.cu, bgk_aux.cu, bgk_mixed.cu).  All enqueue on `stream`.
@@ -120,7 +122,8 @@ int persistent_units(const Params& P, int kind);
 size_t persistent_smem(const Params& P);
 // Resident CTAs of the persistent kernel for dynamic shared memory smem.
 cudaError_t persistent_grid(size_t smem, int* grid);
-constexpr int kMaxPersistInstances = 160;
+constexpr int kMaxPersistInstances = 144;
+static_assert(sizeof(PInstance) * kMaxPersistInstances <= 60 * 1024, "persistent descriptors exceed constant memory");
 // Copy ninst descriptors (device memory) to the kernel's constant array.
 cudaError_t upload_persistent(const PInstance* d_inst, int ninst, cudaStream_t stream);
 cudaError_t launch_persistent(int ninst, int total_units, int nsteps, GridBarrier* bar, int* gerr,
@@ -169,7 +172,7 @@ cudaError_t prepare_step_mixed(const Params& P, int prec);
 // velocities per streaming thread (FP32 state, 2D).
 bool mixed_pipe_preferred(const Params& P);
 cudaError_t launch_step_mixed(const Params& P, int prec, const MixedTables& M, const void* fin, void* fout,
-                              double4_32a* mom, int* err, cudaStream_t stream);
+                              double4_32a* mom, int* err, cudaStream_t stream, int parity);
 cudaError_t launch_to_f64(const Params& P, int prec, const MixedTables& M, const void* f, double2* out,
                           cudaStream_t stream);
 cudaError_t launch_from_f64(const Params& P, int prec, const MixedTables& M, const double2* in, void* f,

@@ -578,13 +578,20 @@ __device__ __forceinline__ unsigned bf16x2_sr(float2 v, unsigned salt) {
   return __byte_perm(ug + (k & 0xFFFFu), uh + (k >> 16), 0x7632);
 }
 
+// The dither's salt: the velocity point's position plus the step counter
+// times 2^32 / golden ratio, so that a value that recurs step after step
+// (a nearly stationary deviation) meets a different dither every step;
+// with the position alone it would be rounded the same way every step and
+// updates below half an ulp would be lost for good.
 template <int PREC>
-__device__ __forceinline__ void store_result(void* fout, size_t c0, int j0, int ng, const float2 (&r)[4]) {
+__device__ __forceinline__ void store_result(void* fout, size_t c0, int j0, int ng, const float2 (&r)[4],
+                                             unsigned step) {
   if (PREC == PREC_BF16) {
     const size_t idx = c0 + j0;
+    const unsigned salt = (unsigned)idx + step * 0x9E3779B9u;
     unsigned w[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) w[p] = bf16x2_sr(r[p], (unsigned)(idx + p));
+    for (int p = 0; p < 4; ++p) w[p] = bf16x2_sr(r[p], salt + (unsigned)p);
     *reinterpret_cast<uint4*>(static_cast<unsigned*>(fout) + idx) = make_uint4(w[0], w[1], w[2], w[3]);
   } else {
     Store<PREC>::store4(fout, c0, j0, ng, r);
@@ -592,6 +599,17 @@ __device__ __forceinline__ void store_result(void* fout, size_t c0, int j0, int 
 }
 
 }  // namespace
+
+// Step counter of the BF16 dither: every CTA reads word `parity`, one
+// thread writes the next value to the other word for the next step's
+// kernel (which reads it with the opposite parity).
+template <int PREC>
+__device__ __forceinline__ unsigned step_counter(const MixedTables& M, int parity) {
+  if (PREC != PREC_BF16 || !M.step_ctr) return 0u;
+  const unsigned c = *(volatile const unsigned*)(M.step_ctr + parity);
+  if (blockIdx.x == 0 && threadIdx.x == 0) M.step_ctr[parity ^ 1] = c + 1u;
+  return c;
+}
 
 // Shared scratch of one block of G cells (WPC = 8/G warps per cell).
 template <int G>
@@ -607,7 +625,8 @@ struct MixedShared {
 template <int PREC, int G, int MGL>
 __device__ __forceinline__ void mixed2d_block(const Params& P, const MixedTables& M, const void* __restrict__ fin,
                                               void* __restrict__ fout, float2* __restrict__ msum,
-                                              int* __restrict__ err, int blk, float* phx, MixedShared<G>& S) {
+                                              int* __restrict__ err, int blk, float* phx, MixedShared<G>& S,
+                                              unsigned step) {
   constexpr int WPC = 8 / G;
   float* phy = phx + G * P.nvx;
   auto& s_part = S.part;
@@ -692,7 +711,7 @@ __device__ __forceinline__ void mixed2d_block(const Params& P, const MixedTables
       const int j0 = 4 * g;
       float2 r[4] = {ft[k][0], ft[k][1], ft[k][2], ft[k][3]};
       if (ok) relax_group<PREC>(M, px, py, j0, a, kappa, r);
-      store_result<PREC>(fout, C.c0, j0, ngroups, r);
+      store_result<PREC>(fout, C.c0, j0, ngroups, r, step);
     }
   }
 }
@@ -703,10 +722,11 @@ __device__ __forceinline__ void mixed2d_block(const Params& P, const MixedTables
 template <int PREC, int G, int MGL>
 __global__ void __launch_bounds__(256, (PREC == PREC_F32 && MGL >= 6) ? 2 : 3)
     step_mixed_kernel(const void* __restrict__ fin, void* __restrict__ fout, float2* __restrict__ msum,
-                      const Params P, const MixedTables M, int* __restrict__ err) {
+                      const Params P, const MixedTables M, int* __restrict__ err, int parity) {
   extern __shared__ float4 smemf4[];
   __shared__ MixedShared<G> S;
-  mixed2d_block<PREC, G, MGL>(P, M, fin, fout, msum, err, blockIdx.x, reinterpret_cast<float*>(smemf4), S);
+  const unsigned step = step_counter<PREC>(M, parity);
+  mixed2d_block<PREC, G, MGL>(P, M, fin, fout, msum, err, blockIdx.x, reinterpret_cast<float*>(smemf4), S, step);
 }
 
 // ---- 2D, one cell at a time, pipelined ----------------------------------------
@@ -762,7 +782,7 @@ constexpr int pipe_threads() { return 32 * (NSW + kPipeMath); }
 template <int PREC, int MGL, int NSW>
 __global__ void __launch_bounds__(pipe_threads<NSW>(), NSW == 8 ? 3 : 4)
     step_mixed_pipe_kernel(const void* __restrict__ fin, void* __restrict__ fout, float2* __restrict__ msum,
-                           const Params P, const MixedTables M, int* __restrict__ err) {
+                           const Params P, const MixedTables M, int* __restrict__ err, int parity) {
   constexpr int NT = 32 * (NSW + 1);
   constexpr int NST = 32 * NSW;
   extern __shared__ float4 smemf4[];
@@ -809,6 +829,7 @@ __global__ void __launch_bounds__(pipe_threads<NSW>(), NSW == 8 ? 3 : 4)
   }
 
   const int tid = threadIdx.x;
+  const unsigned step = step_counter<PREC>(M, parity);
   int b = 0;
   size_t prev_c0 = 0;
   bool have_prev = false;
@@ -853,7 +874,7 @@ __global__ void __launch_bounds__(pipe_threads<NSW>(), NSW == 8 ? 3 : 4)
           float2 r[4];
           unpack_f32(flo[g], fhi[g], r);
           if (cp.ok) relax_group<PREC>(M, px, py, 4 * g, cp.a, cp.kappa, r);
-          store_result<PREC>(fout, prev_c0, 4 * g, ngroups, r);
+          store_result<PREC>(fout, prev_c0, 4 * g, ngroups, r, step);
         }
       }
     }
@@ -1040,7 +1061,7 @@ template <int G, int MGL>
 __device__ __forceinline__ void unit2d(const PInstance& I, const void* fin, void* fout, int blk, float* phx,
                                        char* raw) {
   mixed2d_block<PREC_F32, G, MGL>(I.P, I.M, fin, fout, I.msum, I.err, blk, phx,
-                                  *reinterpret_cast<MixedShared<G>*>(raw));
+                                  *reinterpret_cast<MixedShared<G>*>(raw), 0u);
 }
 __device__ __forceinline__ void unit1d(const PInstance& I, const void* fin, void* fout, int blk) {
   mixed1d_unit(I, fin, fout, blk);
@@ -1327,21 +1348,21 @@ size_t mixed_smem(const Params& P, int G, int) { return mixed_factor_bytes(P, G)
 
 template <int PREC, int G, int MGL>
 cudaError_t launch_mg(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
-                      int* err, cudaStream_t stream) {
+                      int* err, cudaStream_t stream, int parity) {
   const int ncell = P.nx * P.ny;
   const unsigned grid = (unsigned)((ncell + G - 1) / G);
   const size_t smem = mixed_smem(P, G, PREC);
-  step_mixed_kernel<PREC, G, MGL><<<grid, 256, smem, stream>>>(fin, fout, msum, P, M, err);
+  step_mixed_kernel<PREC, G, MGL><<<grid, 256, smem, stream>>>(fin, fout, msum, P, M, err, parity);
   return cudaGetLastError();
 }
 
 template <int PREC, int G>
 cudaError_t dispatch_mgl(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
-                         int* err, cudaStream_t stream) {
+                         int* err, cudaStream_t stream, int parity) {
   switch (P.mgl) {
-    case 2: return launch_mg<PREC, G, 2>(P, M, fin, fout, msum, err, stream);
-    case 4: return launch_mg<PREC, G, 4>(P, M, fin, fout, msum, err, stream);
-    case 6: return launch_mg<PREC, G, 6>(P, M, fin, fout, msum, err, stream);
+    case 2: return launch_mg<PREC, G, 2>(P, M, fin, fout, msum, err, stream, parity);
+    case 4: return launch_mg<PREC, G, 4>(P, M, fin, fout, msum, err, stream, parity);
+    case 6: return launch_mg<PREC, G, 6>(P, M, fin, fout, msum, err, stream, parity);
   }
   return cudaErrorInvalidValue;
 }
@@ -1355,7 +1376,7 @@ int pipe_groups(const Params& P, int nsw) {
 
 template <int PREC, int MGL, int NSW>
 cudaError_t launch_pipe(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
-                        int* err, cudaStream_t stream) {
+                        int* err, cudaStream_t stream, int parity) {
   const size_t smem = pipe_smem_bytes(P);
   int dev = 0, per_sm = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1370,7 +1391,8 @@ cudaError_t launch_pipe(const Params& P, const MixedTables& M, const void* fin, 
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int ncell = P.nx * P.ny;
   const int grid = per_sm * sms < ncell ? per_sm * sms : ncell;
-  step_mixed_pipe_kernel<PREC, MGL, NSW><<<grid, pipe_threads<NSW>(), smem, stream>>>(fin, fout, msum, P, M, err);
+  step_mixed_pipe_kernel<PREC, MGL, NSW><<<grid, pipe_threads<NSW>(), smem, stream>>>(fin, fout, msum, P, M, err,
+                                                                                       parity);
   return cudaGetLastError();
 }
 
@@ -1378,24 +1400,24 @@ cudaError_t launch_pipe(const Params& P, const MixedTables& M, const void* fin, 
 // (the same arithmetic).
 template <int PREC>
 cudaError_t dispatch_tile1(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
-                           int* err, cudaStream_t stream) {
+                           int* err, cudaStream_t stream, int parity) {
   if (pipe_smem_bytes(P) <= kPipeMaxSmem) switch (pipe_groups(P, 8)) {
-      case 1: return launch_pipe<PREC, 1, 8>(P, M, fin, fout, msum, err, stream);
-      case 2: return launch_pipe<PREC, 2, 8>(P, M, fin, fout, msum, err, stream);
-      case 3: return launch_pipe<PREC, 3, 8>(P, M, fin, fout, msum, err, stream);
-      case 4: return launch_pipe<PREC, 4, 8>(P, M, fin, fout, msum, err, stream);
+      case 1: return launch_pipe<PREC, 1, 8>(P, M, fin, fout, msum, err, stream, parity);
+      case 2: return launch_pipe<PREC, 2, 8>(P, M, fin, fout, msum, err, stream, parity);
+      case 3: return launch_pipe<PREC, 3, 8>(P, M, fin, fout, msum, err, stream, parity);
+      case 4: return launch_pipe<PREC, 4, 8>(P, M, fin, fout, msum, err, stream, parity);
     }
-  return dispatch_mgl<PREC, 1>(P, M, fin, fout, msum, err, stream);
+  return dispatch_mgl<PREC, 1>(P, M, fin, fout, msum, err, stream, parity);
 }
 
 template <int PREC>
 cudaError_t dispatch_m(const Params& P, const MixedTables& M, const void* fin, void* fout, float2* msum,
-                       int* err, cudaStream_t stream) {
+                       int* err, cudaStream_t stream, int parity) {
   switch (P.tile) {
-    case 1: return dispatch_tile1<PREC>(P, M, fin, fout, msum, err, stream);
-    case 2: return dispatch_mgl<PREC, 2>(P, M, fin, fout, msum, err, stream);
-    case 4: return dispatch_mgl<PREC, 4>(P, M, fin, fout, msum, err, stream);
-    case 8: return dispatch_mgl<PREC, 8>(P, M, fin, fout, msum, err, stream);
+    case 1: return dispatch_tile1<PREC>(P, M, fin, fout, msum, err, stream, parity);
+    case 2: return dispatch_mgl<PREC, 2>(P, M, fin, fout, msum, err, stream, parity);
+    case 4: return dispatch_mgl<PREC, 4>(P, M, fin, fout, msum, err, stream, parity);
+    case 8: return dispatch_mgl<PREC, 8>(P, M, fin, fout, msum, err, stream, parity);
   }
   return cudaErrorInvalidValue;
 }
@@ -1423,7 +1445,7 @@ int mixed_groups_per_lane(const Params& P, int tile) {
 cudaError_t prepare_step_mixed(const Params&, int) { return cudaSuccess; }
 
 cudaError_t launch_step_mixed(const Params& P, int prec, const MixedTables& M, const void* fin, void* fout,
-                              double4_32a* mom, int* err, cudaStream_t stream) {
+                              double4_32a* mom, int* err, cudaStream_t stream, int parity) {
   float2* msum = reinterpret_cast<float2*>(mom);  // 32 bytes per cell either way
   if (P.dim == 1) {
     const unsigned grid = (unsigned)((P.nx + 7) / 8);
@@ -1434,8 +1456,8 @@ cudaError_t launch_step_mixed(const Params& P, int prec, const MixedTables& M, c
     else step_mixed1d_kernel<4><<<grid, 256, 0, stream>>>(fi, fo, msum, P, M, err);
     return cudaGetLastError();
   }
-  return prec == PREC_F32 ? dispatch_m<PREC_F32>(P, M, fin, fout, msum, err, stream)
-                          : dispatch_m<PREC_BF16>(P, M, fin, fout, msum, err, stream);
+  return prec == PREC_F32 ? dispatch_m<PREC_F32>(P, M, fin, fout, msum, err, stream, parity)
+                          : dispatch_m<PREC_BF16>(P, M, fin, fout, msum, err, stream, parity);
 }
 
 }  // namespace bgk

@@ -111,7 +111,9 @@ def test_cavity256_prefix_against_oracle(prec):
     for k, v in err.items():
         assert v <= b[k], (prec, k, v, b[k])
     if prec == "f64":
-        # the other wall fluxes of the lid per face cell
+        # the other wall fluxes of the lid per face cell, relative to the
+        # size of the one-sided fluxes (the normal momentum flux, about 0.5;
+        # the net mass flux itself is zero to rounding)
+        scale = np.abs(lid[:, 3]).max()
         for col in (1, 3, 4):
-            scale = max(np.abs(lid[:, col]).max(), 1e-3)
-            assert np.abs(fl[:, col - 1] - lid[:, col]).max() <= 1e-12 * scale
+            assert np.abs(fl[:, col - 1] - lid[:, col]).max() <= 1e-12 * scale, col
