@@ -59,7 +59,7 @@ struct bgk_solver {
   double4_32a* mom_tmp = nullptr;   // scratch for bgk_moments(which = 0)
   double4_32a* flux_tmp = nullptr;  // scratch for bgk_wall_fluxes
   double* cx = nullptr;
-  double* cy = nullptr;
+  double* cy = nullptr;  // [2 nvy]: centres, then their squares
   double4_32a* coef = nullptr;
   int* shift = nullptr;
   double2* cxy = nullptr;
@@ -87,6 +87,7 @@ struct bgk_solver {
     bgk::Tables T;
     T.cx = cx;
     T.cy = cy;
+    T.cy2 = cy + P.nvy;
     T.coef = coef;
     T.shift = shift;
     T.cxy = cxy;
@@ -512,7 +513,7 @@ bgk_status bgk_create(const bgk_config* cfg, bgk_solver** out) {
   ALLOC(mom_tmp, ncell);
   ALLOC(flux_tmp, nfc);
   ALLOC(cx, P.nvx);
-  ALLOC(cy, P.nvy);
+  ALLOC(cy, 2 * (size_t)P.nvy);
   ALLOC(coef, P.nv);
   ALLOC(shift, P.nv);
   ALLOC(cxy, P.nv);
@@ -845,7 +846,7 @@ extern "C" bgk_status bgk_step_noalloc(const bgk_config* cfg, const double* f_in
     off = align256(off + bytes);
     return at;
   };
-  const size_t o_cx = take(sizeof(double) * P.nvx), o_cy = take(sizeof(double) * P.nvy);
+  const size_t o_cx = take(sizeof(double) * P.nvx), o_cy = take(sizeof(double) * 2 * P.nvy);
   const size_t o_coef = take(sizeof(double4_32a) * P.nv), o_shift = take(sizeof(int) * P.nv);
   const size_t o_cxy = take(sizeof(double2) * P.nv), o_vinfo = take(sizeof(int) * P.nv);
   const size_t o_ghost = take(sizeof(double2) * bgk::kFaces * P.nv);
@@ -880,6 +881,7 @@ extern "C" bgk_status bgk_step_noalloc(const bgk_config* cfg, const double* f_in
   int* err = (int*)(base + o_err);
   T.cx = cx;
   T.cy = cy;
+  T.cy2 = cy + P.nvy;
   T.coef = coef;
   T.shift = shift;
   T.cxy = cxy;

@@ -21,6 +21,7 @@ __global__ void tables_kernel(const Params P, double* cx, double* cy, double4_32
   const double cyj = (P.dim == 2) ? centre(P.vy_min, jy, P.dcy) : 0.0;
   if (jy == 0) cx[jx] = cxj;
   if (jx == 0) cy[jy] = cyj;
+  if (jx == 0) cy[P.nvy + jy] = __dmul_rn(cyj, cyj);  // c_y^2 after the centres
   const double c2 = __dadd_rn(__dmul_rn(cxj, cxj), __dmul_rn(cyj, cyj));
   cxy[j] = make_double2(cxj, cyj);
   const int sgx = cxj > 0.0 ? 1 : (cxj < 0.0 ? -1 : 0);

@@ -133,6 +133,7 @@ __device__ __forceinline__ bool moments_ok(const double q[4]) {
 struct EffState {
   double base[4], p[4];
   double ib0, ith, isq;  // 1 / n_b, 1 / theta_b, 1 / sqrt(theta_b)
+  double iq0, iq3, ivs;  // the same at the target q (the first base point)
   int it;
   bool conv, fail, reeval;
 };
@@ -148,6 +149,9 @@ __device__ __forceinline__ void eff_set_base(EffState& E) {
 __device__ __forceinline__ void eff_init(EffState& E, const double q[4], bool done) {
   for (int k = 0; k < 4; ++k) E.base[k] = E.p[k] = q[k];
   eff_set_base(E);
+  E.iq0 = E.ib0;
+  E.iq3 = E.ith;
+  E.ivs = E.isq;
   E.it = 0;
   E.conv = done;
   E.fail = false;
@@ -159,7 +163,7 @@ __device__ __forceinline__ void eff_iterate(const Params& P, const double q[4], 
                                             const double My[5], EffState& E, double lin_max = kLinMax,
                                             double tol = kEffTol) {
   // the convergence test scales n by q_n, U by sqrt(q_theta), theta by q_theta
-  const double iq0 = 1.0 / q[0], iq3 = 1.0 / q[3], ivs = sqrt(iq3);
+  const double iq0 = E.iq0, iq3 = E.iq3, ivs = E.ivs;
   double* p = E.p;
   double* b = E.base;
   while (!E.conv && !E.fail && !E.reeval) {
@@ -196,7 +200,10 @@ __device__ __forceinline__ void eff_iterate(const Params& P, const double q[4], 
     }
     if (!(p[0] > 0.0) || !(p[3] > 0.0) || !isfinite(r)) {
       E.fail = true;
-    } else if (r < tol) {
+    } else if (r < tol || (E.it == 1 && 100.0 * r * r < tol)) {
+      // the map p -> D(p) - p changes by the quadrature defect, so the
+      // iteration contracts by about the size r of its first update: after a
+      // first update r the next one is about r^2, below the tolerance here
       E.conv = true;
     } else if (E.it >= kEffMaxIt) {
       if (r < kEffFail) E.conv = true;

@@ -44,6 +44,7 @@ struct Params {
 struct Tables {
   const double* cx;       // [nvx] velocity-cell centres
   const double* cy;       // [nvy] (dim 1: one entry, 0)
+  const double* cy2;      // [nvy] c_y^2 (stored right after cy)
   const double4_32a* coef;    // [nv] (a0, ax, ay, |c|^2): streaming weights, 2D
                           //      (w_near, w_far, 0, c_x^2): 1D
   const int* shift;       // [nv] 1D integer Courant shift [C] (0 in 2D)

@@ -54,9 +54,10 @@ __device__ __forceinline__ double2 ghost_at(const Params& P, const Tables& T, in
 // 16 h + l takes the rows jy = h, h + 2, ... and in each row the columns
 // jx = l + 16 m (m < NM).  A lane's columns never change, so sum c_x g and
 // the c_x^2 part of sum |c|^2 g follow from its column sums after the loop,
-// and sum c_y g and the c_y^2 part from its row sum once per row: per point
-// one FP64 add into the column sum, one into the row sum (NM - 1 per row)
-// and one for h, plus three operations per row: 11/3 at NM = 3 instead of 5.
+// and sum c_y g and the c_y^2 part (c_y^2 from a table) from its row sum once
+// per row: per point one FP64 add into the column sum, one into the row sum
+// (NM - 1 per row) and one for h, plus two per row: 10/3 at NM = 3 instead
+// of 5.
 template <int NM>
 __device__ __forceinline__ void stream_interior_rows(const Params& P, const Tables& T,
                                                      const double2* __restrict__ fc, ptrdiff_t row,
@@ -76,7 +77,7 @@ __device__ __forceinline__ void stream_interior_rows(const Params& P, const Tabl
   for (int jy = lane >> 4; jy < P.nvy; jy += 2) {
     const int j0 = jy * nvx + l;
     const ptrdiff_t offy = -(ptrdiff_t)vi_sy(T.vinfo[j0]) * row;
-    const double cy = T.cy[jy];
+    const double cy = T.cy[jy], cy2 = T.cy2[jy];
     double rg = 0.0;
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
@@ -94,7 +95,7 @@ __device__ __forceinline__ void stream_interior_rows(const Params& P, const Tabl
       sh += ft.y;
     }
     sy = fma(cy, rg, sy);
-    syy = fma(cy * cy, rg, syy);
+    syy = fma(cy2, rg, syy);
   }
   double sxx = 0.0;
 #pragma unroll
@@ -379,45 +380,17 @@ __device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, co
   }
 }
 
-}  // namespace
-
-// 4 cells per CTA (the automatic choice) runs 8 CTAs per SM at 64
-// registers: spilling a little beats 4 CTAs at 124 registers (measured:
-// 204 -> 191 us on 64^2 x 32^2, 5.14 -> 4.84 ms on 256^2 x 48^2; 5 and 6
-// CTAs were slower).
-template <int DIM, int G>
-__global__ void __launch_bounds__(32 * G, G == 4 ? 8 : 1)
-    step_f64_kernel(const double2* __restrict__ fin, double2* __restrict__ fout,
-                    double4_32a* __restrict__ mom, double4_32a* __restrict__ par, const Params P,
-                    const Tables T, int* __restrict__ err) {
-  extern __shared__ double4_32a smem4[];
-  double* phx = reinterpret_cast<double*>(smem4);
-  double* phy = phx + G * P.nvx;
-  __shared__ double s_sum[G][4];
-  __shared__ double s_b[G], s_k[G];
-  __shared__ int s_ok[G];
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// ---- phase 3 ---------------------------------------------------------------
+// A4 for the warp's cell: f^{n+1} = b f~ + a Phi from the f~ parked in the
+// cell's output slots, a Phi_g = px[jx] py[jy], a Phi_h = kappa a Phi_g.
+template <int DIM>
+__device__ __forceinline__ void relax_cell(const Params& P, const Tables& T, double2* __restrict__ fout, int cell,
+                                           const double* __restrict__ px, const double* __restrict__ py, double b,
+                                           double kappa, bool ok) {
+  const int lane = threadIdx.x & 31;
   const int nv = P.nv;
-  const int cell = blockIdx.x * G + warp;
-  const bool live = cell < P.nx * P.ny;
-  // f~ of the warp's cell is parked in the cell's own output slots between
-  // the passes (each lane rereads only what it wrote; the values come back
-  // from L2): staging it in shared memory (16 B per velocity) held an SM to
-  // 3 CTAs, measured 21 % (64^2 x 32^2) and 40 % (256^2 x 48^2) slower
-  double2* tile = fout + (size_t)cell * nv;
-
-  if (live) stream_cell<DIM>(P, T, fin, cell, tile, s_sum[warp]);
-  __syncthreads();
-  if (warp == 0) maxwellian_cells<DIM, G>(P, T, blockIdx.x * G, s_sum, phx, phy, s_b, s_k, s_ok, mom, par, err);
-  __syncthreads();
-  if (!live) return;
-
-  const double b = s_b[warp], kappa = s_k[warp];
-  const bool ok = s_ok[warp] != 0;
-  const double* px = phx + warp * P.nvx;
-  const double* py = phy + warp * P.nvy;
   double2* __restrict__ fo = fout + (size_t)cell * nv;
+  const double2* tile = fo;
   if (DIM == 2 && ok && (P.nvx == 48 || P.nvx == 64)) {
     // rows jy = h, h + 2, ..., columns jx = l + 16 m of lane 16 h + l, as
     // in stream_interior_rows: a Phi = px[jx] py[jy] from shared memory
@@ -451,6 +424,44 @@ __global__ void __launch_bounds__(32 * G, G == 4 ? 8 : 1)
     }
     fo[j] = r;
   }
+}
+
+}  // namespace
+
+// 4 cells per CTA (the automatic choice) runs 8 CTAs per SM at 64
+// registers: spilling a little beats 4 CTAs at 124 registers (measured:
+// 204 -> 191 us on 64^2 x 32^2, 5.14 -> 4.84 ms on 256^2 x 48^2; 5 and 6
+// CTAs were slower).
+template <int DIM, int G>
+__global__ void __launch_bounds__(32 * G, G == 4 ? 8 : 1)
+    step_f64_kernel(const double2* __restrict__ fin, double2* __restrict__ fout,
+                    double4_32a* __restrict__ mom, double4_32a* __restrict__ par, const Params P,
+                    const Tables T, int* __restrict__ err) {
+  extern __shared__ double4_32a smem4[];
+  double* phx = reinterpret_cast<double*>(smem4);
+  double* phy = phx + G * P.nvx;
+  __shared__ double s_sum[G][4];
+  __shared__ double s_b[G], s_k[G];
+  __shared__ int s_ok[G];
+
+  const int warp = threadIdx.x >> 5;
+  const int nv = P.nv;
+  const int cell = blockIdx.x * G + warp;
+  const bool live = cell < P.nx * P.ny;
+  // f~ of the warp's cell is parked in the cell's own output slots between
+  // the passes (each lane rereads only what it wrote; the values come back
+  // from L2): staging it in shared memory (16 B per velocity) held an SM to
+  // 3 CTAs, measured 21 % (64^2 x 32^2) and 40 % (256^2 x 48^2) slower
+  double2* tile = fout + (size_t)cell * nv;
+
+  if (live) stream_cell<DIM>(P, T, fin, cell, tile, s_sum[warp]);
+  __syncthreads();
+  if (warp == 0) maxwellian_cells<DIM, G>(P, T, blockIdx.x * G, s_sum, phx, phy, s_b, s_k, s_ok, mom, par, err);
+  __syncthreads();
+  if (!live) return;
+
+  relax_cell<DIM>(P, T, fout, cell, phx + warp * P.nvx, phy + warp * P.nvy, s_b[warp], s_k[warp],
+                  s_ok[warp] != 0);
 }
 
 namespace {

@@ -228,6 +228,30 @@ def test_cavity256_one_step_full_size():
     s.close()
 
 
+def test_f64_ragged_grid_48_columns():
+    # 130 x 121 cells (3933 CTAs of 4 cells, the last one with 2) with 48 x 48
+    # velocities (the row mapping of the interior cells); three steps, whole
+    # state and the post-streaming moments
+    w = W.scaled(W.CAVITY_256, n=130)
+    prob0, _, _ = oracle.cavity_problem(**w)
+    cfg = solver.cavity_config(**w)
+    cfg.ny = 121
+    cfg.ly = cfg.ly * 121 / 130
+    oc = oracle.make_config(dim=2, nx=130, ny=121, lx=cfg.lx, ly=cfg.ly, nvx=48, nvy=48, vx=(-5, 5), vy=(-5, 5),
+                            cfl=0.5, bc_kind=(1, 1, 1, 1), bc_state=prob0.cfg.bc_state)
+    prob = oracle.Problem(oc)
+    xi = W.perturbation(4, prob.ncell, prob.nv)
+    g, h = oracle.init_uniform(prob, (1.0, 0.0, 0.0, 1.0), xi, 1e-3)
+    s = solver.Solver(cfg)
+    s.init_uniform((1.0, 0.0, 0.0, 1.0), xi, 1e-3)
+    assert s.info.tile_cells == 4
+    s.step(3)
+    g1, h1, mom = oracle.step(prob, g, h, 3)
+    assert_state_close(s.get_state(), g1, h1)
+    assert_moments_close(s.moments(which=1), mom, vscale=0.05)
+    s.close()
+
+
 # ---------------------------------------------------------------------------
 # Edge cases and invariants
 # ---------------------------------------------------------------------------
