@@ -428,12 +428,12 @@ __device__ __forceinline__ void relax_cell(const Params& P, const Tables& T, dou
 
 }  // namespace
 
-// 4 cells per CTA (the automatic choice) runs 8 CTAs per SM at 64
-// registers: spilling a little beats 4 CTAs at 124 registers (measured:
-// 204 -> 191 us on 64^2 x 32^2, 5.14 -> 4.84 ms on 256^2 x 48^2; 5 and 6
-// CTAs were slower).
+// 4 cells per CTA runs 8 CTAs per SM at 64 registers: spilling a little
+// beats 4 CTAs at 124 registers (measured: 204 -> 191 us on 64^2 x 32^2,
+// 5.14 -> 4.84 ms on 256^2 x 48^2; 5 and 6 CTAs were slower); 8 cells per
+// CTA run 4 CTAs per SM at 64 registers (the choice for large 2D grids).
 template <int DIM, int G>
-__global__ void __launch_bounds__(32 * G, G == 4 ? 8 : 1)
+__global__ void __launch_bounds__(32 * G, G == 4 ? 8 : (G == 8 ? 4 : 1))
     step_f64_kernel(const double2* __restrict__ fin, double2* __restrict__ fout,
                     double4_32a* __restrict__ mom, double4_32a* __restrict__ par, const Params P,
                     const Tables T, int* __restrict__ err) {

@@ -228,11 +228,12 @@ def test_cavity256_one_step_full_size():
     s.close()
 
 
-def test_f64_ragged_grid_48_columns():
-    # 130 x 121 cells (3933 CTAs of 4 cells, the last one with 2) with 48 x 48
-    # velocities (the row mapping of the interior cells); three steps, whole
-    # state and the post-streaming moments
-    w = W.scaled(W.CAVITY_256, n=130)
+@pytest.mark.parametrize("tile", [4, 8])
+def test_f64_ragged_grid_48_columns(tile):
+    # 130 x 121 cells (3933 CTAs of 4 cells, the last one with 2; or 1967 of
+    # 8, the last one with 2) with 48 x 48 velocities (the row mapping of the
+    # interior cells); three steps, whole state and the post-streaming moments
+    w = W.scaled(W.CAVITY_256, n=130, tile_cells=tile)
     prob0, _, _ = oracle.cavity_problem(**w)
     cfg = solver.cavity_config(**w)
     cfg.ny = 121
@@ -244,7 +245,7 @@ def test_f64_ragged_grid_48_columns():
     g, h = oracle.init_uniform(prob, (1.0, 0.0, 0.0, 1.0), xi, 1e-3)
     s = solver.Solver(cfg)
     s.init_uniform((1.0, 0.0, 0.0, 1.0), xi, 1e-3)
-    assert s.info.tile_cells == 4
+    assert s.info.tile_cells == tile
     s.step(3)
     g1, h1, mom = oracle.step(prob, g, h, 3)
     assert_state_close(s.get_state(), g1, h1)
