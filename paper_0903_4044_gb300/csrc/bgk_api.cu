@@ -293,13 +293,14 @@ bgk_status validate(const bgk_config* c, bgk::Params* P, double* max_courant) {
 
 // Largest tile (cells per CTA) that keeps two CTAs' shared memory within an
 // SM and still gives every SM at least two CTAs.  FP64 takes 8 cells per CTA
-// (4 CTAs per SM) only in 2D with at least four full waves of them: the
+// (4 CTAs per SM) only in 2D with at least three full waves of them: the
 // per-cell solve then serves 8 cells per warp instruction (measured 2.6 %
-// faster on 256^2 x 48^2); on fewer cells the last wave leaves SMs idle
-// (7 % slower on 64^2 x 32^2), and 4 cells per CTA are kept.
+// faster on 256^2 x 48^2, and 2.8 % on the gradient of the 128^2 x 32^2
+// cavity); on fewer cells the last wave leaves SMs idle (7 % slower on
+// 64^2 x 32^2), and 4 cells per CTA are kept.
 int auto_tile(const bgk::Params& P, int prec, int sms) {
   const long long ncell = (long long)P.nx * P.ny;
-  if (prec == BGK_F64 && P.dim == 2 && ncell >= 8LL * 4 * 4 * sms && step_smem(P, prec, 8) <= kAutoSmem) return 8;
+  if (prec == BGK_F64 && P.dim == 2 && ncell >= 8LL * 4 * 3 * sms && step_smem(P, prec, 8) <= kAutoSmem) return 8;
   // FP32, 2D, at least 3 groups of 4 velocities per streaming thread: the
   // pipelined one-cell kernel (measured 9 % faster than 2 cells per CTA on
   // 256^2 x 48^2; slower on 64^2 x 32^2 and in BF16)
