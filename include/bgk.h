@@ -339,7 +339,10 @@ BGK_API bgk_status bgk3v_sync(bgk3v_solver* s);
  * nsteps steps from the solver's current state f0.  Runs the steps forward
  * (saving the state every checkpoint_every steps), then backward segment by
  * segment, recomputing each segment's states from its checkpoint: device
- * memory of about (nsteps / checkpoint_every + checkpoint_every + 3) states.
+ * memory of about (nsteps / checkpoint_every + checkpoint_every + 3) states;
+ * checkpoint_every = 0 takes ceil(sqrt(nsteps)), which minimises it (about
+ * 92 states instead of 123 for 2000 steps at 100).  The checkpoint spacing does
+ * not change the results.
  * Outputs: out = {J, dJ/d ln L, dJ/dU_W}, where L scales the domain and,
  * through the Courant rule, the time step together (Kn = 1/L for the
  * cavity: dJ/dKn = -(dJ/d ln L)/Kn) and U_W is the lid's (YHI) x speed;

@@ -1393,7 +1393,8 @@ extern "C" bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int c
                                             int on_device, double out[3]) {
   BGK_GUARD_BEGIN
   if (!s || !out) return fail(BGK_ERR_INVALID_ARG, "null argument");
-  if (nsteps < 1 || checkpoint_every < 1) return fail(BGK_ERR_INVALID_ARG, "nsteps and checkpoint_every must be >= 1");
+  if (nsteps < 1 || checkpoint_every < 0)
+    return fail(BGK_ERR_INVALID_ARG, "nsteps must be >= 1 and checkpoint_every >= 0");
   if (s->P.dim != 2 || s->prec != bgk::PREC_F64 || !s->P.relax_exact)
     return fail(BGK_ERR_UNSUPPORTED, "the adjoint needs dim 2, BGK_F64 and exact relaxation");
   if (s->P.bc_kind[bgk::YHI] != BGK_BC_DIFFUSE) return fail(BGK_ERR_UNSUPPORTED, "the adjoint needs a diffuse lid (YHI)");
@@ -1403,7 +1404,15 @@ extern "C" bgk_status bgk_adjoint_lid_shear(bgk_solver* s, int64_t nsteps, int c
   const bgk::Params& P = s->P;
   const bgk::Tables T = s->tables();
   const size_t elems = s->state_elems(), sbytes = sizeof(double2) * elems;
-  const int K = (int)std::min<int64_t>(checkpoint_every, nsteps);
+  // checkpoint_every = 0: K = ceil(sqrt(nsteps)), which minimises the
+  // nsteps / K checkpoints plus the K + 1 states of a segment
+  int64_t k0 = checkpoint_every;
+  if (k0 == 0) {
+    k0 = (int64_t)std::ceil(std::sqrt((double)nsteps));
+    while (k0 * k0 < nsteps) ++k0;
+    while (k0 > 1 && (k0 - 1) * (k0 - 1) >= nsteps) --k0;
+  }
+  const int K = (int)std::min<int64_t>(k0, nsteps);
   const int64_t M = (nsteps + K - 1) / K;
   const int ncell = P.nx * P.ny;
   std::vector<void*> bufs;
