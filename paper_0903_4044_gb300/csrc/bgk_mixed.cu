@@ -560,13 +560,18 @@ __device__ __forceinline__ void cell_factors(const Params& P, const MixedTables&
 }
 
 // Stochastic rounding of an FP32 pair (g, h) to two BF16 values packed in
-// one word: add 16 bits of dither below the kept bits of each value, then
-// keep the top halves.  Rounding up happens with probability equal to the
-// discarded fraction, so the rounding is unbiased and per-step updates
-// smaller than half a BF16 ulp of the deviation survive on average instead
-// of being rounded away every step.  Both dithers come from one 32-bit hash
-// of the pair's bits and its position (a multiply-xorshift mix in the style
-// of MurmurHash3's finaliser): the low half for g, the high half for h.
+// one word: 16 bits of dither are added below the kept bits of each value's
+// magnitude and the top halves kept.  Rounding away from zero happens with
+// probability equal to the discarded fraction, so the rounding is unbiased
+// and per-step updates smaller than half a BF16 ulp of the deviation survive
+// on average instead of being rounded away every step.  Both dithers come
+// from one 32-bit hash of the pair's bits and its position (a
+// multiply-xorshift mix in the style of MurmurHash3's finaliser): the low
+// half for g, the high half for h.  The conversion instruction with the
+// .rs rounding mode (sm_100 and later) does the add, truncate and pack in
+// one; it takes the low 16 random bits for its second operand and the high
+// 16 for its first, the same split as adding the halves by hand (checked
+// bit for bit against that on the GPU).
 __device__ __forceinline__ unsigned bf16x2_sr(float2 v, unsigned salt) {
   const unsigned ug = __float_as_uint(v.x), uh = __float_as_uint(v.y);
   unsigned k = (ug ^ salt) * 0x9E3779B1u + uh;
@@ -575,7 +580,9 @@ __device__ __forceinline__ unsigned bf16x2_sr(float2 v, unsigned salt) {
   k ^= k >> 13;
   k *= 0xC2B2AE35u;
   k ^= k >> 16;
-  return __byte_perm(ug + (k & 0xFFFFu), uh + (k >> 16), 0x7632);
+  unsigned w;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(v.y), "f"(v.x), "r"(k));
+  return w;
 }
 
 // The dither's salt: the velocity point's position plus the step counter

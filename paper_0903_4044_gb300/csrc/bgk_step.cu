@@ -245,6 +245,55 @@ __device__ __forceinline__ void stream_cell(const Params& P, const Tables& T,
 }
 
 // ---- phase 2 ---------------------------------------------------------------
+// Sums of five values over the L lanes of a group (sub = 0 .. L-1, L a power
+// of two >= 4), returned to every lane of the group.  Recursive halving: the
+// first exchange splits the values 3 + 2 between the two halves of the
+// group, the second 2 + 1 within each half, the third leaves one value per
+// lane, then plain butterflies; 8 FP64 additions at L = 32 (5 at L = 4)
+// instead of 5 log2 L.  The lane pattern of each value is fixed, so the
+// result does not depend on the data.
+template <int L>
+__device__ __forceinline__ void group_sum5(double& m0, double& m1, double& m2, double& m3, double& m4,
+                                           int sub) {
+  static_assert(L >= 4 && (L & (L - 1)) == 0, "group of 4, 8, 16 or 32 lanes");
+  constexpr unsigned kAll = 0xffffffffu;
+  const int base = (threadIdx.x & 31) - sub;
+  // 1: the low half keeps (m0, m1, m2), the high half (m3, m4, 0)
+  const bool h1 = sub & (L / 2);
+  double a0 = h1 ? m3 : m0, a1 = h1 ? m4 : m1, a2 = h1 ? 0.0 : m2;
+  const double t0 = h1 ? m0 : m3, t1 = h1 ? m1 : m4, t2 = h1 ? m2 : 0.0;
+  a0 += __shfl_xor_sync(kAll, t0, L / 2);
+  a1 += __shfl_xor_sync(kAll, t1, L / 2);
+  a2 += __shfl_xor_sync(kAll, t2, L / 2);
+  // 2: of (a0, a1, a2) the low quarter keeps (a0, a1), the high one (a2, 0)
+  const bool h2 = sub & (L / 4);
+  double k0 = h2 ? a2 : a0, k1 = h2 ? 0.0 : a1;
+  const double u0 = h2 ? a0 : a2, u1 = h2 ? a1 : 0.0;
+  k0 += __shfl_xor_sync(kAll, u0, L / 4);
+  k1 += __shfl_xor_sync(kAll, u1, L / 4);
+  if (L == 4) {
+    // lane 0: (m0, m1), lane 1: (m2, 0), lane 2: (m3, m4), lane 3: (0, 0)
+    m0 = __shfl_sync(kAll, k0, base);
+    m1 = __shfl_sync(kAll, k1, base);
+    m2 = __shfl_sync(kAll, k0, base + 1);
+    m3 = __shfl_sync(kAll, k0, base + 2);
+    m4 = __shfl_sync(kAll, k1, base + 2);
+    return;
+  }
+  // 3: one value per lane, then the remaining lane bits summed out
+  const bool h3 = sub & (L / 8);
+  double v = h3 ? k1 : k0;
+  v += __shfl_xor_sync(kAll, h3 ? k0 : k1, L / 8);
+#pragma unroll
+  for (int s = L / 16; s > 0; s >>= 1) v += __shfl_xor_sync(kAll, v, s);
+  // m0 at sub 0, m1 at L/8, m2 at L/4, m3 at L/2, m4 at L/2 + L/8
+  m0 = __shfl_sync(kAll, v, base);
+  m1 = __shfl_sync(kAll, v, base + L / 8);
+  m2 = __shfl_sync(kAll, v, base + L / 4);
+  m3 = __shfl_sync(kAll, v, base + L / 2);
+  m4 = __shfl_sync(kAll, v, base + L / 2 + L / 8);
+}
+
 // Exponentials e_j = exp(-(c_j - u)^2 / theta) of one axis for one cell,
 // lanes sub, sub + L, ... of the cell's group; stores them when `store`;
 // returns the group's central sums M_m = sum d^m e, d = c_j - u, m = 0..4.
@@ -253,8 +302,9 @@ __device__ __forceinline__ void stream_cell(const Params& P, const Tables& T,
 // r_{i+1} = r_i exp(-2 D^2 / theta): three exponentials per lane and two
 // products per further point instead of one exponential per point (each
 // product adds a rounding: after k points the relative error is about k^2
-// ulp, 1e-14 at k = 8).  Where e_0 could underflow or r_0 overflow (theta
-// far below the grid's scale) every point takes its own exponential.
+// ulp, 1e-14 at k = 8).  Lanes with fewer than four points, and where e_0
+// could underflow or r_0 overflow (theta far below the grid's scale), take
+// one exponential per point.
 template <int L>
 __device__ __forceinline__ void axis_sums(const double* __restrict__ c, int n, double dc, double u,
                                           double inv_th, int sub, bool store, double* __restrict__ out, bool want,
@@ -264,7 +314,7 @@ __device__ __forceinline__ void axis_sums(const double* __restrict__ c, int n, d
     const double D = L * dc;
     const double d0 = c[sub] - u;
     const double x0 = (d0 * d0) * inv_th, y0 = (2.0 * d0 * D + D * D) * inv_th;
-    const bool rec = x0 < 600.0 && -y0 < 600.0;
+    const bool rec = n >= 4 * L && x0 < 600.0 && -y0 < 600.0;
     double e = exp(-x0);
     double r = rec ? exp(-y0) : 0.0;
     const double q = rec ? exp(-2.0 * D * D * inv_th) : 0.0;
@@ -294,16 +344,7 @@ __device__ __forceinline__ void axis_sums(const double* __restrict__ c, int n, d
       }
     }
   }
-  if (want) {
-#pragma unroll
-    for (int s = 1; s < L; s <<= 1) {
-      m0 += __shfl_xor_sync(0xffffffffu, m0, s);
-      m1 += __shfl_xor_sync(0xffffffffu, m1, s);
-      m2 += __shfl_xor_sync(0xffffffffu, m2, s);
-      m3 += __shfl_xor_sync(0xffffffffu, m3, s);
-      m4 += __shfl_xor_sync(0xffffffffu, m4, s);
-    }
-  }
+  if (want) group_sum5<L>(m0, m1, m2, m3, m4, sub);
   M[0] = m0;
   M[1] = m1;
   M[2] = m2;
@@ -355,7 +396,7 @@ __device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, co
     // A4 factors: a Phi_g = px[jx] py[jy], moved from E.base to p
     double w1x, w1y, w2;
     eff_lin(E, w1x, w1y, w2);
-    const double pref = (DIM == 1) ? p[0] / sqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
+    const double pref = (DIM == 1) ? p[0] * rsqrt(kPi() * p[3]) : p[0] / (kPi() * p[3]);
     const double ap = a * pref;
     for (int j = sub; j < P.nvx; j += L) {
       const double d = T.cx[j] - E.base[1];
