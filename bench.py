@@ -56,21 +56,21 @@ CAVITY256_200 = "cavity_kn0.05_ma0.05_256x256_v48x48_200steps"
 # capture commands sit with the ncu summaries under profiles/.
 MEASURED_TRAFFIC = {
     ("cavity_kn0.1_ma0.1_64x64_v32x32_f64", "f64"): {
-        "bytes": 167.9e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
-        "sha1": "2da3275d16898163ba0a53c9871800d09cd32d4c", "kernel": "bgk::step_f64_kernel"},
-    # captured on 128^2 x 48^2 at 8 cells per CTA (2.448 GB per launch,
+        "bytes": 167.5e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
+        "sha1": "4ad418a895b5d49188a26ad90a488440abc5aae3", "kernel": "bgk::step_f64_kernel"},
+    # captured on 128^2 x 48^2 at 8 cells per CTA (2.450 GB per launch,
     # 64.9 B per update: the parked f~ of the resident cells exceeds L2 at
     # 48^2 velocities) and scaled by the 4x updates of a 256^2 x 48^2 launch
     (CAVITY256_200, "f64"): {
-        "bytes": 4 * 2.448e9, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
-        "sha1": "2da3275d16898163ba0a53c9871800d09cd32d4c", "kernel": "bgk::step_f64_kernel",
+        "bytes": 4 * 2.450e9, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
+        "sha1": "4ad418a895b5d49188a26ad90a488440abc5aae3", "kernel": "bgk::step_f64_kernel",
         "note": "captured on 128^2 x 48^2 cells x velocities at 8 cells per CTA, scaled by updates"},
     (CAVITY256_200, "f32"): {
-        "bytes": 2.554e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
-        "sha1": "b5150188ce32896947a6b44c5f3f06a8300fe3a6", "kernel": "bgk::step_mixed_pipe_kernel"},
+        "bytes": 2.511e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
+        "sha1": "be172c107906990b571b7c8e9164677410bc9d27", "kernel": "bgk::step_mixed_pipe_kernel"},
     (CAVITY256_200, "bf16"): {
-        "bytes": 1.174e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
-        "sha1": "b5150188ce32896947a6b44c5f3f06a8300fe3a6", "kernel": "bgk::step_mixed_kernel"},
+        "bytes": 1.173e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
+        "sha1": "be172c107906990b571b7c8e9164677410bc9d27", "kernel": "bgk::step_mixed_kernel"},
 }
 
 
