@@ -40,7 +40,7 @@ bgk_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 constexpr int kChunk = 64;  // steps per captured graph (even: ends on the same buffer)
-constexpr size_t kMaxSmem = 226 * 1024;   // dynamic shared memory one CTA may use (227 KB minus static)
+constexpr size_t kMaxSmem = 224 * 1024;   // dynamic shared memory one CTA may use (227 KB minus static, at most 3 KB)
 constexpr size_t kAutoSmem = 113 * 1024;  // automatic tiles leave room for two CTAs per SM
 
 }  // namespace

@@ -421,6 +421,120 @@ __device__ void maxwellian_cells(const Params& P, const Tables& T, int cell0, co
   }
 }
 
+// Phase 2 of a 2D CTA on two warps: the y-axis Gaussian sums and factors of
+// the G cells run on warp 1 (another SM sub-partition) while warp 0 does the
+// x axis and the scalar solve, so the CTA's other warps wait at the barrier
+// for about one axis less.  Every value is computed by the same functions in
+// the same order as in maxwellian_cells, so the results are the same bit
+// for bit.  Warp 0 hands warp 1 the base point of each round and the factor
+// update; warp 1 hands back the y central sums (named barrier 1, 64 threads).
+template <int G>
+struct SolveXchg {
+  double ub[G], ith[G];  // y base velocity and 1 / theta_b of the round
+  double my[G][5];       // y central sums of the round
+  double w1y[G], w2[G];  // factor update (after the last round)
+  int need[G], ok[G];
+  int go;
+};
+
+__device__ __forceinline__ void pair_barrier() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+template <int G>
+__device__ void maxwellian_cells_2w(const Params& P, const Tables& T, int cell0, const double (*sums)[4],
+                                    double* __restrict__ phx, double* __restrict__ phy, double* sb, double* sk,
+                                    int* sok, double4_32a* __restrict__ mom, double4_32a* __restrict__ par,
+                                    int* __restrict__ err, SolveXchg<G>& X) {
+  constexpr int L = 32 / G;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c = lane / L, sub = lane % L;
+  const bool cons = P.conservative != 0;
+  if (warp == 1) {
+    double* py = phy + c * P.nvy;
+    for (;;) {
+      pair_barrier();  // base point of the round published
+      if (!X.go) break;
+      const bool need = X.need[c] != 0;
+      double Mt[5];
+      axis_sums<L>(T.cy, P.nvy, P.dcy, X.ub[c], X.ith[c], sub, need, py, cons, Mt);
+      if (sub == 0)
+        for (int m = 0; m < 5; ++m) X.my[c][m] = Mt[m];
+      pair_barrier();  // sums handed over
+    }
+    pair_barrier();  // factor update published
+    if (X.ok[c]) {
+      const double ub = X.ub[c], w1y = X.w1y[c], w2 = X.w2[c];
+      for (int j = sub; j < P.nvy; j += L) {
+        const double d = T.cy[j] - ub;
+        py[j] = py[j] * fma(d, fma(d, w2, w1y), 1.0);
+      }
+    }
+    return;
+  }
+  const int cell = cell0 + c;
+  const bool live = cell < P.nx * P.ny;
+  double qm[4] = {1.0, 0.0, 0.0, 1.0};  // moments of f~ (Eq. macroscopic)
+  if (live) moments_from_sums(sums[c][0], sums[c][1], sums[c][2], sums[c][3], P.dv, qm);
+  bool ok = live && moments_ok(qm);
+  const double q[4] = {ok ? qm[0] : 1.0, ok ? qm[1] : 0.0, ok ? qm[2] : 0.0, ok ? qm[3] : 1.0};
+  double* px = phx + c * P.nvx;
+  EffState E;
+  eff_init(E, q, !(cons && ok));
+  double a = 0.0, b = 0.0;
+  double Mx[5], My[5];
+  // every exit from this loop goes through a published go = 0 (warp 1
+  // leaves its loop on it), so the two warps pass the same barriers
+  for (int round = 0;; ++round) {
+    const bool need = round <= kEffMaxIt && (round == 0 || E.reeval);
+    const bool go = __any_sync(0xffffffffu, need);
+    if (sub == 0) {
+      X.need[c] = need ? 1 : 0;
+      X.ub[c] = E.base[2];
+      X.ith[c] = E.ith;
+    }
+    if (lane == 0) X.go = go ? 1 : 0;
+    pair_barrier();
+    if (!go) break;
+    double Mt[5];
+    axis_sums<L>(T.cx, P.nvx, P.dcx, E.base[1], E.ith, sub, need, px, cons, Mt);
+    if (need)
+      for (int m = 0; m < 5; ++m) Mx[m] = Mt[m];
+    if (round == 0) relax_weights(P, q, a, b);
+    pair_barrier();
+    if (need)
+      for (int m = 0; m < 5; ++m) My[m] = X.my[c][m];
+    E.reeval = false;
+    eff_iterate<2>(P, q, Mx, My, E);  // A3, linearised about E.base
+  }
+  if (E.fail) ok = false;
+  const double* p = E.p;
+  double w1x = 0.0, w1y = 0.0, w2 = 0.0;
+  if (ok) eff_lin(E, w1x, w1y, w2);
+  if (sub == 0) {
+    X.ok[c] = ok ? 1 : 0;
+    X.ub[c] = E.base[2];
+    X.w1y[c] = w1y;
+    X.w2[c] = w2;
+  }
+  pair_barrier();
+  if (ok) {
+    // A4 factors: a Phi_g = px[jx] py[jy], moved from E.base to p
+    const double ap = a * (p[0] / (kPi() * p[3]));
+    for (int j = sub; j < P.nvx; j += L) {
+      const double d = T.cx[j] - E.base[1];
+      px[j] = ap * (px[j] * fma(d, fma(d, w2, w1x), 1.0));
+    }
+  }
+  if (sub == 0) {
+    sb[c] = b;
+    sk[c] = 0.5 * p[3];
+    sok[c] = ok ? 1 : 0;
+    if (live) {
+      mom[cell] = make_double4_32a(qm[0], qm[1], qm[2], qm[3]);
+      if (par) par[cell] = make_double4_32a(p[0], p[1], p[2], p[3]);
+      if (!ok) atomicOr(err, E.fail ? ERR_EFFECTIVE : ERR_MOMENT);
+    }
+  }
+}
+
 // ---- phase 3 ---------------------------------------------------------------
 // A4 for the warp's cell: f^{n+1} = b f~ + a Phi from the f~ parked in the
 // cell's output slots, a Phi_g = px[jx] py[jy], a Phi_h = kappa a Phi_g.
@@ -497,7 +611,12 @@ __global__ void __launch_bounds__(32 * G, G == 4 ? 8 : (G == 8 ? 4 : 1))
 
   if (live) stream_cell<DIM>(P, T, fin, cell, tile, s_sum[warp]);
   __syncthreads();
-  if (warp == 0) maxwellian_cells<DIM, G>(P, T, blockIdx.x * G, s_sum, phx, phy, s_b, s_k, s_ok, mom, par, err);
+  if (DIM == 2 && G >= 2) {
+    __shared__ SolveXchg<G> s_x;
+    if (warp < 2) maxwellian_cells_2w<G>(P, T, blockIdx.x * G, s_sum, phx, phy, s_b, s_k, s_ok, mom, par, err, s_x);
+  } else if (warp == 0) {
+    maxwellian_cells<DIM, G>(P, T, blockIdx.x * G, s_sum, phx, phy, s_b, s_k, s_ok, mom, par, err);
+  }
   __syncthreads();
   if (!live) return;
 
@@ -521,12 +640,19 @@ cudaError_t launch_g(const Params& P, const Tables& T, const double2* fin, doubl
 }
 
 // The attribute belongs to the kernel, not to a solver: set it to the
-// largest dynamic shared memory any solver may request (226 KB) so that
-// solvers with different grids sharing an instantiation never shrink it.
+// largest dynamic shared memory any solver may request (what the device
+// allows a CTA beside the kernel's static shared memory) so that solvers
+// with different grids sharing an instantiation never shrink it.
 template <int DIM, int G>
 cudaError_t prepare_g(const Params&) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, step_f64_kernel<DIM, G>);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(step_f64_kernel<DIM, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              226 * 1024);
+                              optin - (int)fa.sharedSizeBytes);
 }
 
 template <int DIM>
