@@ -11,7 +11,8 @@
 //         neighbours come from L2, boundary values from the ghost tables;
 //         f~ is parked in the cell's output slots until phase 3;
 //     A2  FP64 velocity sums of f~ for Eq. (macroscopic), one warp reduction;
-//   phase 2 (warp 0, the G cells in lanes)
+//   phase 2 (warp 0, the G cells in lanes; in 2D warp 1 takes the y axis of
+//            the Gaussian sums and factors)
 //     A3  moments, nu = n theta^(1-omega), relaxation weights and the
 //         effective Maxwellian parameters (one set of exponentials per cell,
 //         linearised updates), separable factors written to shared memory;
