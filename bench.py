@@ -56,14 +56,14 @@ CAVITY256_200 = "cavity_kn0.05_ma0.05_256x256_v48x48_200steps"
 # capture commands sit with the ncu summaries under profiles/.
 MEASURED_TRAFFIC = {
     ("cavity_kn0.1_ma0.1_64x64_v32x32_f64", "f64"): {
-        "bytes": 170.5e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
-        "sha1": "06a4261cd4fb32a5e30e128c3fc27fd456606f83", "kernel": "bgk::step_f64_kernel"},
-    # captured on 128^2 x 48^2 at 8 cells per CTA (2.457 GB per launch,
+        "bytes": 170.2e6, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
+        "sha1": "c04036d50a56b465b9502fa52f0cd08b44b65df3", "kernel": "bgk::step_f64_kernel"},
+    # captured on 128^2 x 48^2 at 8 cells per CTA (2.458 GB per launch,
     # 65.1 B per update: the parked f~ of the resident cells exceeds L2 at
     # 48^2 velocities) and scaled by the 4x updates of a 256^2 x 48^2 launch
     (CAVITY256_200, "f64"): {
-        "bytes": 4 * 2.457e9, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
-        "sha1": "06a4261cd4fb32a5e30e128c3fc27fd456606f83", "kernel": "bgk::step_f64_kernel",
+        "bytes": 4 * 2.458e9, "sources": ("csrc/bgk_step.cu", "csrc/bgk_device.cuh"),
+        "sha1": "c04036d50a56b465b9502fa52f0cd08b44b65df3", "kernel": "bgk::step_f64_kernel",
         "note": "captured on 128^2 x 48^2 cells x velocities at 8 cells per CTA, scaled by updates"},
     (CAVITY256_200, "f32"): {
         "bytes": 2.511e9, "sources": ("csrc/bgk_mixed.cu", "csrc/bgk_device.cuh"),
