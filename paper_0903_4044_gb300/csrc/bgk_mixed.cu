@@ -1163,11 +1163,13 @@ int persistent_kind(const Params& P) {
     if (P.nvx > 128) return -1;
     return P.nvx <= 32 ? PK_1D_K1 : P.nvx <= 64 ? PK_1D_K2 : PK_1D_K4;
   }
+  // the persistent kernel carries kinds of 2 and 4 groups per lane
   const int m = mixed_groups_per_lane(P, P.tile);
+  const bool m4 = m == 3 || m == 4;
   switch (P.tile) {
-    case 1: return m == 2 ? PK_2D_G1_M2 : m == 4 ? PK_2D_G1_M4 : -1;
-    case 2: return m == 2 ? PK_2D_G2_M2 : m == 4 ? PK_2D_G2_M4 : -1;
-    case 4: return m == 2 ? PK_2D_G4_M2 : m == 4 ? PK_2D_G4_M4 : -1;
+    case 1: return m == 2 ? PK_2D_G1_M2 : m4 ? PK_2D_G1_M4 : -1;
+    case 2: return m == 2 ? PK_2D_G2_M2 : m4 ? PK_2D_G2_M4 : -1;
+    case 4: return m == 2 ? PK_2D_G4_M2 : m4 ? PK_2D_G4_M4 : -1;
     case 8: return m == 2 ? PK_2D_G8_M2 : -1;
   }
   return -1;
@@ -1368,7 +1370,9 @@ cudaError_t dispatch_mgl(const Params& P, const MixedTables& M, const void* fin,
                          int* err, cudaStream_t stream, int parity) {
   switch (P.mgl) {
     case 2: return launch_mg<PREC, G, 2>(P, M, fin, fout, msum, err, stream, parity);
+    case 3: return launch_mg<PREC, G, 3>(P, M, fin, fout, msum, err, stream, parity);
     case 4: return launch_mg<PREC, G, 4>(P, M, fin, fout, msum, err, stream, parity);
+    case 5: return launch_mg<PREC, G, 5>(P, M, fin, fout, msum, err, stream, parity);
     case 6: return launch_mg<PREC, G, 6>(P, M, fin, fout, msum, err, stream, parity);
   }
   return cudaErrorInvalidValue;
@@ -1437,14 +1441,18 @@ bool mixed_pipe_preferred(const Params& P) {
 
 size_t step_mixed_smem_bytes(const Params& P, int tile, int prec) { return mixed_smem(P, tile, prec); }
 
-// Groups of 4 velocities per lane when a cell has 256/tile lanes, rounded up
-// to an instantiated count (2, 4 or 6); 0 if more than 6 would be needed.
+// Groups of 4 velocities per lane when a cell has 256/tile lanes (at least
+// 2); 0 if more than 6 would be needed.  Every count from 2 to 6 is
+// instantiated: the f~ a lane keeps in registers is sized by it, and one
+// group too many cost registers (BF16 at 4.5 groups per lane: 64 bytes of
+// spills and 0.798 ms per 256^2 x 48^2 step at 6, 16 bytes and 0.771 ms at
+// 5).  The count does not change the arithmetic (a lane's groups and their
+// order are the same), only which registers hold them.
 int mixed_groups_per_lane(const Params& P, int tile) {
   const int lanes = 256 / tile;
   const int need = (P.nv / 4 + lanes - 1) / lanes;
   if (need <= 2) return 2;
-  if (need <= 4) return 4;
-  if (need <= 6) return 6;
+  if (need <= 6) return need;
   return 0;
 }
 
