@@ -111,8 +111,9 @@ typedef struct {
   int32_t precision;    /* bgk_precision */
   int32_t tile_cells;   /* spatial cells per CTA of the step kernel: 0 = chosen
                            by the library, else 1, 2, 4 or 8 (tuning knob; the
-                           results do not depend on it beyond the rounding
-                           order of reduced-precision sums; for 2D FP32 and
+                           results do not depend on it beyond rounding: the
+                           order of the per-cell sums and, in FP64, how the
+                           per-cell Gaussian factors are formed; for 2D FP32 and
                            BF16 states, 1 runs the pipelined one-cell kernel
                            when its buffers fit, with the one-cell block's
                            results) */
