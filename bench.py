@@ -3,10 +3,20 @@
 One benchmark "step" is one whole run of the workload: reset the state to
 the seeded initial condition, then the workload's number of time steps
 (each: streaming, moments, Maxwellian, relaxation, boundaries).  Default
-workload: the 2D lid-driven cavity, Kn 0.1, lid Mach 0.1, 64x64 cells, 32x32
-velocities, FP64, 5000 time steps.
+workload: the 2D lid-driven cavity, Kn 0.05, lid Mach 0.05, 256x256 cells,
+48x48 velocities, its first 200 time steps in FP64; the same line carries
+the FP32 and BF16-deviation forms of that run (`forms`, with their errors
+against the oracle's stored fields after 2000 steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Workloads: cavity256 (default), cavity256_full (all 20000 steps), cavity64
+(64x64 cells, 32x32 velocities, 5000 steps), shock (200 cells, 64
+velocities, 4000 steps), batch (64 cavities and 16 shocks; --persistent for
+the single-launch form), adjoint (gradient of the lid shear, 128x128 x
+32x32, 2000 steps), shock3v / shock3v_m15 (full 3D velocity grid), dsweep
+(drag and flow rate against rarefaction); --precision f32 / bf16 for the
+reduced forms, --accuracy for the per-field errors of a whole run.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on
 the host cores instead (bounded samples of the same workload).  With N > 1
